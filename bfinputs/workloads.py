@@ -1,0 +1,90 @@
+"""Workload sizes and seeded random draws (no butterfly arithmetic here).
+
+Workloads follow the paper's Example 1 (1D FIO, Sec. 4) and the sizes the
+library is benchmarked at.  Every random array is drawn from a numpy PCG64
+stream keyed by (seed, tag), so each array can be regenerated on its own.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from .factors import ButterflyFactors, tree_sizes
+
+
+@dataclass(frozen=True)
+class Config:
+    name: str
+    L: int
+    n0: int
+    r: int
+    kind: str          # entry function of the oracle construction ("fio" or "dft")
+    nrhs: tuple
+    seed: int = 0
+
+    @property
+    def N(self) -> int:
+        return self.n0 << self.L
+
+
+CONFIGS = {
+    # 1D FIO, N = 4096, depth 8 (16 points per leaf), rank 12, one RHS, seed 0.
+    "fio_n4096_r12": Config("fio_n4096_r12", L=8, n0=16, r=12, kind="fio", nrhs=(1,)),
+    # 1D FIO at N = 2^20, depth 16 (16 points per leaf), rank 16.
+    "fio_n1m_r16": Config("fio_n1m_r16", L=16, n0=16, r=16, kind="fio", nrhs=(1, 8, 64, 256)),
+    # 1D FIO at N = 2^18, depth 14, rank 16, 32 RHS.
+    "fio_n256k_r16": Config("fio_n256k_r16", L=14, n0=16, r=16, kind="fio", nrhs=(32,)),
+}
+
+
+def _rng(seed: int, *tag: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed)] + [int(t) for t in tag])
+
+
+def complex_normal(shape, seed: int, tag: int = 0, dtype=np.complex128) -> np.ndarray:
+    """I.i.d. standard complex normal entries CN(0, 1): real and imaginary
+    parts independent N(0, 1/2)."""
+    rng = _rng(seed, 7919, tag)
+    n = int(np.prod(shape))
+    fdt = np.float32 if np.dtype(dtype) == np.complex64 else np.float64
+    x = rng.standard_normal(2 * n, dtype=fdt)
+    x *= fdt(np.sqrt(0.5))
+    return x.view(np.dtype(dtype)).reshape(shape)
+
+
+def _cn(rng: np.random.Generator, shape, scale: float, dtype) -> np.ndarray:
+    n = int(np.prod(shape))
+    fdt = np.float32 if np.dtype(dtype) == np.complex64 else np.float64
+    x = rng.standard_normal(2 * n, dtype=fdt)
+    x *= fdt(scale * np.sqrt(0.5))
+    return x.view(np.dtype(dtype)).reshape(shape)
+
+
+def synthetic_factors(L: int, n0: int, r: int, seed: int = 0,
+                      dtype=np.complex64) -> ButterflyFactors:
+    """Seeded random factors with the block shapes of a depth-L, leaf-n0,
+    rank-r butterfly factorization.
+
+    Entries are i.i.d. complex normal with variances 1/n0 (V^L), 1/(2r) (H, G)
+    and 1/r (U^L), and S uniform on [0.5, 1.5]; with these scales every factor
+    preserves the expected squared norm of the vector it is applied to.  The
+    cost of an apply does not depend on the values, so these stand in for a
+    constructed factorization wherever only the shapes matter.
+    """
+    s = tree_sizes(L, n0, r)
+    nb, h, m = s["nblocks"], s["h"], s["m"]
+    VL = _cn(_rng(seed, 1), (nb, n0, r), 1.0 / np.sqrt(n0), dtype)
+    UL = _cn(_rng(seed, 2), (nb, n0, r), 1.0 / np.sqrt(r), dtype)
+    H = [_cn(_rng(seed, 3, t), (nb, r, 2 * r), 1.0 / np.sqrt(2 * r), dtype) for t in range(h)]
+    G = [_cn(_rng(seed, 4, t), (nb, r, 2 * r), 1.0 / np.sqrt(2 * r), dtype) for t in range(h)]
+    rdt = np.float32 if np.dtype(dtype) == np.complex64 else np.float64
+    S = _rng(seed, 5).uniform(0.5, 1.5, size=(m, m, r)).astype(rdt)
+    return ButterflyFactors(L, n0, r, VL, H, S, G, UL,
+                            meta={"source": "synthetic", "seed": seed}).validate()
+
+
+def sample_rows(N: int, count: int = 256, seed: int = 0) -> np.ndarray:
+    """A sorted random set of ``count`` distinct rows (the set S of the
+    accuracy measure epsilon^a in Sec. 4 has 256 points)."""
+    return np.sort(_rng(seed, 31337).choice(N, size=min(count, N), replace=False))

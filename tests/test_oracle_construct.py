@@ -1,0 +1,103 @@
+"""Pins of the oracle construction (Sec. 3) against the dense product, the FFT,
+the exact special case r >= block size, and the complementary low-rank
+property (Sec. 1.1) measured by full SVDs."""
+import numpy as np
+import pytest
+
+from bfinputs import complex_normal, sample_rows
+from oracle import apply as A
+from oracle import construct as C
+from oracle import kernel as K
+from oracle import sparse as SP
+
+
+@pytest.mark.parametrize("N,L,r,kind", [(64, 4, 16, "fio"), (64, 2, 32, "fio"), (64, 4, 16, "dft"),
+                                        (8, 0, 8, "fio"), (128, 6, 16, "fio")])
+def test_exact_when_rank_covers_blocks(N, L, r, kind):
+    """With r >= N/2^h every middle block and every 2r-column stack is kept at
+    full rank, so the factorization is exact up to rounding."""
+    F = C.construct(N, L, r, kind, seed=1)
+    Kd = K.dense_matrix(N, kind)
+    assert np.linalg.norm(SP.dense_product(F) - Kd) / np.linalg.norm(Kd) < 1e-12
+    g = complex_normal((N, 2), seed=2)
+    assert K.rel_err(A.bf_apply(F, g), Kd @ g) < 1e-12
+    assert K.rel_err(A.bf_adjoint(F, g), Kd.conj().T @ g) < 1e-12
+
+
+@pytest.mark.parametrize("N,L,r", [(256, 8, 8), (1024, 10, 10), (1024, 8, 12)])
+def test_dft_factorization_against_fft(N, L, r):
+    """Fourier matrix (Sec. 1.1): the factorization reproduces N ifft(g) (-1)^j
+    within 10 eps of the construction (eps as recorded by the construction)."""
+    F = C.construct(N, L, r, "dft", seed=0)
+    g = complex_normal((N,), seed=0)
+    err = K.rel_err(A.bf_apply(F, g), K.dft_closed_form(g, N))
+    assert err <= 10 * F.meta["eps"]
+    assert err < 1e-5
+
+
+@pytest.mark.parametrize("N,L,r", [(1024, 10, 4), (1024, 10, 8), (4096, 8, 12)])
+def test_fio_factorization_within_construction_eps(N, L, r):
+    """Example 1: epsilon^a on 256 random rows (Sec. 4) <= 10 eps."""
+    F = C.construct(N, L, r, "fio", seed=0)
+    g = complex_normal((N,), seed=0)
+    S = sample_rows(N, 256, seed=0)
+    err = K.rel_err(A.bf_apply(F, g)[S], K.dense_apply(g, N, "fio", rows=S))
+    assert err <= 10 * F.meta["eps"]
+
+
+def test_fio_accuracy_improves_with_rank_and_not_with_n():
+    """Sec. 4 observations on Table 1: the accuracy is controlled by r and is
+    almost independent of N at fixed r (Table 1 itself grows by up to ~2x per
+    quadrupling of N at r = 8; the bound here is 4x; leaf size 1)."""
+    errs = {}
+    for N in (256, 1024):
+        for r in (4, 6, 8):
+            F = C.construct(N, int(np.log2(N)), r, "fio", seed=0)
+            g = complex_normal((N,), seed=1)
+            errs[N, r] = K.rel_err(A.bf_apply(F, g), K.dense_apply(g, N, "fio"))
+    for N in (256, 1024):
+        assert errs[N, 4] > 10 * errs[N, 6] > 100 * errs[N, 8]
+    for r in (4, 6, 8):
+        assert 1 / 4 < errs[1024, r] / errs[256, r] < 4
+
+
+@pytest.mark.parametrize("kind", ["fio", "dft"])
+def test_complementary_low_rank_ranks_do_not_grow_with_n(kind):
+    """Sec. 1.1: for A at level l of T_X and B at level L-l of T_Omega, K_{A,B}
+    has an epsilon-rank bounded independently of N (leaf size fixed at 1)."""
+    eps = 1e-6
+    maxrank = {}
+    for N in (64, 256, 1024):
+        L = int(np.log2(N))
+        worst = 0
+        for l in range(1, L):
+            ni, nj = 1 << l, 1 << (L - l)
+            for i in sorted({0, ni // 2, ni - 1}):
+                for j in sorted({0, nj // 2, nj - 1}):
+                    s = C.block_singular_values(N, L, l, i, j, kind)
+                    worst = max(worst, int(np.sum(s > eps * s[0])))
+        maxrank[N] = worst
+    assert maxrank[64] == maxrank[256] == maxrank[1024] or \
+        max(maxrank.values()) - min(maxrank.values()) <= 1
+    assert max(maxrank.values()) <= 12
+
+
+def test_memory_saving_order_reproduces_middle_blocks():
+    """Sec. 3.3: recomputing each middle block in the V pass (per-block seeds)
+    gives exactly the factors of the cached order."""
+    F1 = C.construct(256, 8, 6, "fio", seed=3, cache_middle=True)
+    F2 = C.construct(256, 8, 6, "fio", seed=3, cache_middle=False)
+    for a, b in [(F1.VL, F2.VL), (F1.UL, F2.UL), (F1.S, F2.S)] + list(zip(F1.H, F2.H)) + list(zip(F1.G, F2.G)):
+        assert np.array_equal(a, b)
+
+
+def test_middle_level_blocks_match_eq_kequmv():
+    """Sec. 3.1: U^h_{i,j} S^h_{i,j} (V^h_{j,i})^* approximates K^h_{i,j}."""
+    N, L, r = 256, 4, 12
+    for i, j in [(0, 0), (1, 3), (3, 2)]:
+        U, S, V, res = C.middle_block(N, L, r, i, j, "fio", seed=0)
+        nb = N // 4
+        Z = K.entries(i * nb + np.arange(nb), j * nb + np.arange(nb), N, "fio")
+        sv = np.linalg.svd(Z, compute_uv=False)
+        err = np.linalg.norm(Z - (U * S) @ V.conj().T, 2)
+        assert err < 10 * sv[r]
