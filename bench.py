@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Butterfly-factorization apply benchmark on GB300.
+
+One step = bf_apply (u = K_bf g) then bf_apply_adjoint (v = K_bf^* u) on a batch
+of nrhs complex64 vectors: one pass of the whole hot path (leaf, transfer
+levels, middle transpose, transfer levels, leaf; forward and adjoint).  The
+workload is the 1D-FIO-shaped factorization with N = 2^20, L = 16 (leaf 16),
+r = 16, with seeded synthetic factor values (the apply's cost does not depend
+on them).  Metric: vectors through K or K^* per second, whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--nrhs B] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun each rank applies its own batch
+with its own copy of the factors (independent problems: weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "butterfly apply vectors/s at N=2^20 r=16 (apply + adjoint, complex64)"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--workload", default="fio_n1m_r16")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--sweep", default="8,64,256", help="extra nrhs values reported in nrhs_sweep ('' = none)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return args
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def aggregate(ms_by_rank, vectors_per_rank):
+    """Whole-job throughput: all ranks' vectors over the slowest rank's time."""
+    ms = max(ms_by_rank)
+    return sum(vectors_per_rank) / (ms / 1e3), ms
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_config(cfg, nrhs):
+    return {
+        "workload": f"{cfg.name}: butterfly factorization of a 1D-FIO-shaped N=2^{cfg.L + (cfg.n0.bit_length() - 1)} "
+                    f"matrix, L={cfg.L}, leaf={cfg.n0}, r={cfg.r}, seeded synthetic factor values",
+        "N": cfg.N, "L": cfg.L, "leaf": cfg.n0, "r": cfg.r, "nrhs": nrhs,
+        "step": "bf_apply then bf_apply_adjoint on nrhs vectors (2*nrhs vectors per step)",
+        "l2": "inputs larger than L2: 9.13 GB of packed factors streamed per step",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", device_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        inside = [p for t, p in self.samples if t0 <= t <= t1] or [p for t, p in self.samples]
+        if not inside:
+            return None
+        mhz = [num(p[1]) for p in inside if num(p[1]) is not None]
+        mx = [num(p[2]) for p in inside if num(p[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in inside:
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inside),
+                "power_w_max": max((num(p[3]) or 0.0) for p in inside)}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1502_01379_gb300 as bf
+    from bfinputs import CONFIGS, complex_normal, synthetic_factors
+
+    from paper_1502_01379_gb300 import build as pkg_build
+    pkg_build.build()
+    cfg = CONFIGS[args.workload]
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sweep = [int(s) for s in args.sweep.split(",") if s.strip()] if args.sweep else []
+    nrhs = args.nrhs
+    nrhs_max = max([nrhs] + sweep)
+    F = synthetic_factors(cfg.L, cfg.n0, cfg.r, seed=args.seed, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=nrhs_max)
+    N, h, nb, n0, r, m = F.N, F.h, 1 << F.L, F.n0, F.r, F.m
+    stream = torch.cuda.current_stream()
+
+    def batch(n, seed):
+        return torch.from_numpy(complex_normal((n, N), seed=seed, dtype=np.complex64)).to(dev)
+
+    g = batch(nrhs, 1000 + rank)
+    u = torch.empty_like(g)
+    v = torch.empty_like(g)
+
+    def step(x, y, z, n):
+        bf.bf_apply(plan, x, y, nrhs=n, stream=stream)
+        bf.bf_apply_adjoint(plan, y, z, nrhs=n, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(x, y, z, n, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(x, y, z, n)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            bf.bf_plan_kernel_times(plan)          # reset
+            bf.bf_plan_set_profiling(plan, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(x, y, z, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kt = None
+        if profile:
+            bf.bf_plan_set_profiling(plan, False)
+            kt = bf.bf_plan_kernel_times(plan)
+        barrier()
+        ms_all = ms
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_all = float(t.item())
+        bf.bf_plan_check(plan)
+        return ms_all, kt
+
+    # ---- headline: device-resident inputs
+    dev_id = str(local)
+    try:
+        dev_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not dev_id.startswith("GPU-"):
+            dev_id = "GPU-" + dev_id
+    except Exception:
+        pass
+    sampler = ClockSampler(dev_id) if rank == 0 else None
+    t_clk0 = time.time()
+    ms, kt = timed(g, u, v, nrhs, args.steps, args.warmup, profile=True)
+    t_clk1 = time.time()
+    if sampler:
+        sampler.stop()
+    value, ms_tot = aggregate([ms], [2 * nrhs * args.steps * world])
+    ms_per_step = ms_tot / args.steps
+
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
+    chunks = -(-nrhs // nrhs_max)
+    transfer = h * nb * 2 * r * r * 8
+    leaf = nb * n0 * r * 8
+    vec = N * min(nrhs, nrhs_max) * 8
+    alg = {"down": leaf + transfer + vec, "up": transfer + leaf + m * m * r * 4 + vec}
+    names = {"down": "bf_down_kernel", "up": "bf_up_kernel"}
+    kernels = {}
+    for k, (launches, kms) in kt.items():
+        avg_s = kms / launches / 1e3
+        kernels[k] = {"name": names[k], "launches": launches, "avg_us": avg_s * 1e6,
+                      "alg_bytes_per_launch": alg[k], "achieved_gbs": alg[k] / avg_s / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_us"] * kernels[k]["launches"])
+    peak, peak_src = load_peaks()
+    traffic = load_traffic(names[dom])
+    roof = {"bound": "hbm", "kernel": names[dom], "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
+            "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / peak, "peak_source": peak_src,
+            "traffic": traffic,
+            "bytes_note": "per launch: leaf n0*r + L/2 levels of 2^L r x 2r blocks (complex64) + S + one N-vector per RHS"}
+
+    # ---- e2e through the C ABI with pinned host buffers
+    gh = g.cpu().pin_memory()
+    uh = torch.empty_like(gh).pin_memory()
+    vh = torch.empty_like(gh).pin_memory()
+    ms_e2e, _ = timed(gh, uh, vh, nrhs, max(3, args.steps // 2), 3)
+    steps_e2e = max(3, args.steps // 2)
+    e2e_value, _ = aggregate([ms_e2e], [2 * nrhs * steps_e2e * world])
+
+    # ---- nrhs sweep (same plan)
+    sweep_out = []
+    for n in sweep:
+        gs = batch(n, 2000 + n)
+        us, vs = torch.empty_like(gs), torch.empty_like(gs)
+        st = 5
+        ms_s, _ = timed(gs, us, vs, n, st, 3)
+        val, _ = aggregate([ms_s], [2 * n * st * world])
+        sweep_out.append({"nrhs": n, "vectors_per_s": val, "ms_per_step": ms_s / st})
+        del gs, us, vs
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(cfg, nrhs),
+        "roofline": roof,
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": "vectors/s", "h2d_bytes_per_step": 2 * N * nrhs * 8,
+                "d2h_bytes_per_step": 2 * N * nrhs * 8},
+        "gpu_launches": 4 * chunks * args.steps,
+        "clocks": sampler.summary(t_clk0, t_clk1) if sampler else None,
+        "nrhs_sweep": sweep_out,
+        "plan_device_gb": bf.bf_plan_device_bytes(plan) / 1e9,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(F, g[0].cpu().numpy(), u[0].cpu().numpy(), args.cpu_seconds)
+    plan.destroy()
+    return out
+
+
+def load_traffic(kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (hash recorded beside it); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1502_01379_gb300", "csrc", "bf_kernels.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = d.get(kernel_name)
+    if not ent or ent.get("kernel_source_sha256_16") != digest:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(F, g0, u_gpu0, seconds):
+    """The FP64 oracle (plain C loops, OpenMP) on this host's cores: apply +
+    adjoint of one vector, repeated for about `seconds`."""
+    import numpy as np
+
+    from oracle import capply
+    from oracle.kernel import rel_err
+    P = capply.PreparedFactors(F)
+    capply.bf_apply_c(P, g0)                          # warm-up
+    n = 0
+    t0 = time.time()
+    while True:
+        u = capply.bf_apply_c(P, g0)
+        capply.bf_adjoint_c(P, u)
+        n += 1
+        if time.time() - t0 >= seconds and n >= 2:
+            break
+    dt = time.time() - t0
+    return {"value": 2 * n / dt, "unit": "vectors/s", "cores": capply.num_threads(), "kind": "oracle",
+            "sample": f"{n} x (apply + adjoint) of one RHS at the full workload size, FP64, {dt:.1f} s",
+            "rel_err_vs_gpu_apply": rel_err(u_gpu0.astype(np.complex128), u)}
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle as it stands (FP64 C loops on the host cores), same workload;
+    each step applies K and K^* to one of the nrhs vectors (a bounded sample)."""
+    import numpy as np
+
+    from bfinputs import CONFIGS, complex_normal, synthetic_factors
+    from oracle import capply
+    cfg = CONFIGS[args.workload]
+    F = synthetic_factors(cfg.L, cfg.n0, cfg.r, seed=args.seed, dtype=np.complex64)
+    P = capply.PreparedFactors(F)
+    g = complex_normal((F.N,), seed=1000, dtype=np.complex64)
+    for _ in range(args.warmup):
+        capply.bf_adjoint_c(P, capply.bf_apply_c(P, g))
+    t0 = time.time()
+    for _ in range(args.steps):
+        capply.bf_adjoint_c(P, capply.bf_apply_c(P, g))
+    dt = time.time() - t0
+    value = 2 * args.steps / dt
+    cores = capply.num_threads()
+    sample = f"each step: apply + adjoint of 1 of the {args.nrhs} RHS, FP64, full N"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(cfg, args.nrhs),
+            "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -6,6 +6,8 @@ stream keyed by (seed, tag), so each array can be regenerated on its own.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -38,26 +40,42 @@ CONFIGS = {
 }
 
 
+_CHUNK = 1 << 22   # real values per independent stream
+
+
 def _rng(seed: int, *tag: int) -> np.random.Generator:
     return np.random.default_rng([int(seed)] + [int(t) for t in tag])
+
+
+def _normals(n: int, fdt, seed: int, tag: tuple, scale: float) -> np.ndarray:
+    """n i.i.d. N(0, scale^2) reals; chunk c comes from the stream keyed by
+    (seed, *tag, c), so the values do not depend on the thread count."""
+    out = np.empty(n, dtype=fdt)
+
+    def fill(c):
+        part = out[c * _CHUNK:(c + 1) * _CHUNK]
+        _rng(seed, *tag, c).standard_normal(out=part, dtype=fdt)
+        part *= fdt(scale)
+
+    nchunks = (n + _CHUNK - 1) // _CHUNK
+    if nchunks <= 1:
+        fill(0)
+    else:
+        with ThreadPoolExecutor(min(nchunks, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, range(nchunks)))
+    return out
 
 
 def complex_normal(shape, seed: int, tag: int = 0, dtype=np.complex128) -> np.ndarray:
     """I.i.d. standard complex normal entries CN(0, 1): real and imaginary
     parts independent N(0, 1/2)."""
-    rng = _rng(seed, 7919, tag)
-    n = int(np.prod(shape))
-    fdt = np.float32 if np.dtype(dtype) == np.complex64 else np.float64
-    x = rng.standard_normal(2 * n, dtype=fdt)
-    x *= fdt(np.sqrt(0.5))
-    return x.view(np.dtype(dtype)).reshape(shape)
+    return _cn(seed, (7919, tag), shape, 1.0, dtype)
 
 
-def _cn(rng: np.random.Generator, shape, scale: float, dtype) -> np.ndarray:
+def _cn(seed: int, tag: tuple, shape, scale: float, dtype) -> np.ndarray:
     n = int(np.prod(shape))
     fdt = np.float32 if np.dtype(dtype) == np.complex64 else np.float64
-    x = rng.standard_normal(2 * n, dtype=fdt)
-    x *= fdt(scale * np.sqrt(0.5))
+    x = _normals(2 * n, fdt, seed, tag, scale * np.sqrt(0.5))
     return x.view(np.dtype(dtype)).reshape(shape)
 
 
@@ -74,10 +92,10 @@ def synthetic_factors(L: int, n0: int, r: int, seed: int = 0,
     """
     s = tree_sizes(L, n0, r)
     nb, h, m = s["nblocks"], s["h"], s["m"]
-    VL = _cn(_rng(seed, 1), (nb, n0, r), 1.0 / np.sqrt(n0), dtype)
-    UL = _cn(_rng(seed, 2), (nb, n0, r), 1.0 / np.sqrt(r), dtype)
-    H = [_cn(_rng(seed, 3, t), (nb, r, 2 * r), 1.0 / np.sqrt(2 * r), dtype) for t in range(h)]
-    G = [_cn(_rng(seed, 4, t), (nb, r, 2 * r), 1.0 / np.sqrt(2 * r), dtype) for t in range(h)]
+    VL = _cn(seed, (1,), (nb, n0, r), 1.0 / np.sqrt(n0), dtype)
+    UL = _cn(seed, (2,), (nb, n0, r), 1.0 / np.sqrt(r), dtype)
+    H = [_cn(seed, (3, t), (nb, r, 2 * r), 1.0 / np.sqrt(2 * r), dtype) for t in range(h)]
+    G = [_cn(seed, (4, t), (nb, r, 2 * r), 1.0 / np.sqrt(2 * r), dtype) for t in range(h)]
     rdt = np.float32 if np.dtype(dtype) == np.complex64 else np.float64
     S = _rng(seed, 5).uniform(0.5, 1.5, size=(m, m, r)).astype(rdt)
     return ButterflyFactors(L, n0, r, VL, H, S, G, UL,

@@ -1,0 +1,133 @@
+/*
+ * bfly.h -- C ABI of the GB300 butterfly-factorization apply library (libbfly.so).
+ *
+ * The library applies a constructed butterfly factorization
+ *
+ *     K ~ U^L G^{L-1} ... G^h M^h (H^h)^* ... (H^{L-1})^* (V^L)^*          (Eq. Kfactors, Sec. 1.2)
+ *
+ * and its adjoint to batches of complex vectors on one GPU.  K is N x N with
+ * N = n0 * 2^L; the row and column trees T_X, T_Omega are complete binary
+ * trees of even depth L (Sec. 3), h = L/2 and m = 2^h.  The factors are the
+ * ones produced by the construction of Sec. 3: leaf bases U^L, V^L
+ * (2^L blocks of n0 x r), transfer blocks G^l, H^l (2^L blocks of r x 2r per
+ * level l = h..L-1, Eq. RSh2 and Sec. 3.2.2) and the middle-level weights
+ * S^h_{i,j} of M^h (Eq. KeqUMV).  The apply costs O(N log N) per vector
+ * (Sec. 3.3): one pass over every factor.
+ *
+ * All entry points return a bf_status and never throw, abort or print.
+ * Argument errors are reported before anything is launched.  Calls that take
+ * a stream are asynchronous with respect to the host unless stated otherwise.
+ */
+#ifndef BFLY_H
+#define BFLY_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID = 1,      /* bad argument: null pointer, odd L, aliasing in/out, ld < N, ... */
+    BF_ERR_CUDA = 2,         /* a CUDA runtime call failed (the CUDA error is cleared)          */
+    BF_ERR_NOMEM = 3,        /* device or host allocation failed                               */
+    BF_ERR_UNSUPPORTED = 4,  /* valid but outside this build's limits (r > 32, n0 > 64, ...)   */
+    BF_ERR_TIMEOUT = 5,      /* a kernel's bounded wait expired; its output is not valid       */
+} bf_status;
+
+typedef enum {
+    BF_C64 = 1,              /* complex64: interleaved (re, im) float; S as float             */
+    BF_C128 = 2,             /* complex128: interleaved (re, im) double; S as double          */
+} bf_dtype;
+
+/* Shape of a factorization.  Limits of this build: L even, 0 <= L <= 24;
+ * 1 <= r <= 32; 1 <= leaf <= 64; and m * max(leaf, r) <= 8192 (one tree
+ * node's vector segment must fit in shared memory). */
+typedef struct {
+    int L;          /* depth of T_X and T_Omega, even (Sec. 1.2)                     */
+    int leaf;       /* n0 = N / 2^L, points per leaf node (Sec. 3, "bounded leaf")  */
+    int r;          /* rank of every low-rank block (Sec. 3)                         */
+    int nrhs_max;   /* most vectors one kernel pass processes; sizes the workspace   */
+} bf_desc;
+
+/* Host arrays of the factors in canonical layout, row-major, block index
+ * first; all in the dtype given (S real).  h = L/2, m = 2^h, nb = 2^L.
+ *   VL      nb blocks of n0 x r: block b is V^L_{b,0} (column leaf b).
+ *   H[t]    t = 0..h-1 holds level l = h + t: nb blocks of r x 2r; block
+ *           j'*2^{L-l-1} + i is H^l_{j',i} (Sec. 3.2.2).
+ *   S       m*m*r reals: S[(i*m + j)*r + k] is entry k of the diagonal S^h_{i,j}
+ *           (row node i, column node j; Eq. KeqUMV).
+ *   G[t]    as H: block i'*2^{L-l-1} + j is G^l_{i',j} (Eq. RSh2).
+ *   UL      nb blocks of n0 x r: block a is U^L_{a,0}.
+ * For L = 0, H and G may be NULL. */
+typedef struct {
+    int dtype;                  /* bf_dtype */
+    const void *VL;
+    const void *const *H;
+    const void *S;
+    const void *const *G;
+    const void *UL;
+} bf_factors;
+
+typedef struct bf_plan_s *bf_plan;
+
+/* Builds a plan: validates the shape, packs the factors into the device
+ * layouts of the forward and adjoint kernels (complex64, block-contiguous in
+ * the order each thread block consumes them), uploads them, and allocates a
+ * workspace of 2^L * r * nrhs_max complex64 entries.  The factor arrays are
+ * copied: the caller may free them when this returns.  Synchronizes `stream`
+ * before returning.  On error *plan is set to NULL. */
+bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *factors,
+                         cudaStream_t stream);
+
+/* u = K_bf g for nrhs vectors (Eq. Kfactors applied right to left).
+ *   in, out  complex64, column-major N x nrhs with leading dimension ld >= N
+ *            (entries), rows in tree order (1D: natural index order).
+ *            Device pointers are used in place.  Host pointers (pinned or
+ *            pageable) are staged through plan-owned device buffers, which the
+ *            first such call allocates; the host output is complete when
+ *            `stream` completes.
+ *   nrhs     >= 0; 0 is a no-op.  Processed nrhs_max vectors per pass.
+ * in and out must not overlap (BF_ERR_INVALID).  One plan owns one
+ * workspace: calls on the same plan must not run concurrently on different
+ * streams. */
+bf_status bf_apply(bf_plan plan, const void *in, void *out, int nrhs, long long ld,
+                   cudaStream_t stream);
+
+/* g' = K_bf^* f = V^L H^{L-1} ... H^h (M^h)^* (G^h)^* ... (G^{L-1})^* (U^L)^* f,
+ * the conjugate transpose of the factor chain (Eq. Kfactors).  Same
+ * arguments and rules as bf_apply. */
+bf_status bf_apply_adjoint(bf_plan plan, const void *in, void *out, int nrhs, long long ld,
+                           cudaStream_t stream);
+
+/* Releases every device and host resource of the plan (synchronizes the
+ * device first).  NULL is accepted. */
+bf_status bf_plan_destroy(bf_plan plan);
+
+/* Reads and clears the plan's device error word (synchronizes `stream`):
+ * BF_ERR_TIMEOUT if a kernel gave up on a bounded wait since the last check. */
+bf_status bf_plan_check(bf_plan plan, cudaStream_t stream);
+
+/* Bytes of device memory the plan holds (factors, workspace, staging). */
+size_t bf_plan_device_bytes(bf_plan plan);
+
+/* Per-kernel timing for profiling: when enabled, every kernel the plan
+ * launches is bracketed by CUDA events on the launching stream.
+ * bf_plan_kernel_times synchronizes the device and returns, for the
+ * "down" kernel (leaf + merging levels) and the "up" kernel (middle
+ * transpose + splitting levels + leaf), the launch count and summed
+ * milliseconds since the last reset, then resets them. */
+bf_status bf_plan_set_profiling(bf_plan plan, int enable);
+bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms,
+                               int *up_launches, double *up_ms);
+
+/* Static text for a status code. */
+const char *bf_status_string(bf_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFLY_H */

@@ -1,0 +1,192 @@
+"""Thin ctypes binding of libbfly.so (include/bfly.h), same names as the C ABI.
+
+Argument marshalling only: every step of the apply runs in the library's CUDA
+kernels.  Vectors are passed as torch tensors (device or host) or raw
+addresses; a batch of nrhs vectors of length N is a (nrhs, N) complex64
+tensor, i.e. the ABI's column-major N x nrhs layout with ld = N.  Streams are
+torch.cuda.Stream objects, raw cudaStream_t handles, or None for torch's
+current stream.  If the library has not been built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BF_OK, BF_ERR_INVALID, BF_ERR_CUDA, BF_ERR_NOMEM, BF_ERR_UNSUPPORTED, BF_ERR_TIMEOUT = range(6)
+BF_C64, BF_C128 = 1, 2
+
+EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", "bf_plan_check",
+           "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string")
+
+
+class BfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {bf_status_string(status)} (status {status})")
+        self.status = status
+
+
+class bf_desc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("leaf", ctypes.c_int), ("r", ctypes.c_int), ("nrhs_max", ctypes.c_int)]
+
+
+class bf_factors(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("VL", ctypes.c_void_p), ("H", ctypes.POINTER(ctypes.c_void_p)),
+                ("S", ctypes.c_void_p), ("G", ctypes.POINTER(ctypes.c_void_p)), ("UL", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libbfly.so (built in-tree by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libbfly.so not found at {p}: build it with paper_1502_01379_gb300.build.build()")
+    L = ctypes.CDLL(p)
+    vp, i, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "bf_plan_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_desc), ctypes.POINTER(bf_factors), vp]),
+        "bf_apply": (i, [vp, vp, vp, i, ll, vp]),
+        "bf_apply_adjoint": (i, [vp, vp, vp, i, ll, vp]),
+        "bf_plan_destroy": (i, [vp]),
+        "bf_plan_check": (i, [vp, vp]),
+        "bf_plan_device_bytes": (ctypes.c_size_t, [vp]),
+        "bf_plan_set_profiling": (i, [vp, i]),
+        "bf_plan_kernel_times": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
+        "bf_status_string": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def bf_status_string(status: int) -> str:
+    return load().bf_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str) -> None:
+    if status != BF_OK:
+        raise BfError(status, what)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _addr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    return int(x.data_ptr())
+
+
+class Plan:
+    """Owns a bf_plan handle and the host arrays kept alive during creation."""
+
+    def __init__(self, handle: int, N: int, L: int, n0: int, r: int, nrhs_max: int):
+        self.handle, self.N, self.L, self.n0, self.r, self.nrhs_max = handle, N, L, n0, r, nrhs_max
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self) -> None:
+        if getattr(self, "handle", None):
+            load().bf_plan_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def bf_plan_create(factors, nrhs_max: int = 1, stream=None) -> Plan:
+    """Create a plan from factors in canonical layout (any object with L, n0,
+    r, VL, H, S, G, UL as numpy arrays; complex64 or complex128)."""
+    c128 = np.asarray(factors.VL).dtype == np.complex128
+    cdt, rdt = (np.complex128, np.float64) if c128 else (np.complex64, np.float32)
+    keep = [np.ascontiguousarray(factors.VL, cdt), np.ascontiguousarray(factors.UL, cdt),
+            np.ascontiguousarray(factors.S, rdt)]
+    Hs = [np.ascontiguousarray(a, cdt) for a in factors.H]
+    Gs = [np.ascontiguousarray(a, cdt) for a in factors.G]
+    nh = max(1, len(Hs))
+    h_arr = (ctypes.c_void_p * nh)(*[a.ctypes.data for a in Hs])
+    g_arr = (ctypes.c_void_p * nh)(*[a.ctypes.data for a in Gs])
+    f = bf_factors(BF_C128 if c128 else BF_C64, keep[0].ctypes.data,
+                   ctypes.cast(h_arr, ctypes.POINTER(ctypes.c_void_p)), keep[2].ctypes.data,
+                   ctypes.cast(g_arr, ctypes.POINTER(ctypes.c_void_p)), keep[1].ctypes.data)
+    d = bf_desc(int(factors.L), int(factors.n0), int(factors.r), int(nrhs_max))
+    h = ctypes.c_void_p()
+    _check(load().bf_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.byref(f),
+                                 ctypes.c_void_p(_stream_handle(stream))), "bf_plan_create")
+    del keep, Hs, Gs
+    return Plan(h.value, int(factors.n0) << int(factors.L), int(factors.L), int(factors.n0),
+                int(factors.r), int(nrhs_max))
+
+
+def _vec_args(plan: Plan, x, y, nrhs, ld):
+    if nrhs is None:
+        nrhs = 1 if x.ndim == 1 else int(x.shape[0])
+    if ld is None:
+        ld = plan.N
+    return _addr(x), _addr(y), int(nrhs), int(ld)
+
+
+def bf_apply(plan: Plan, x, y, nrhs: int | None = None, ld: int | None = None, stream=None) -> None:
+    """y = K_bf x (asynchronous on `stream`)."""
+    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
+    _check(load().bf_apply(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi), n, l,
+                           ctypes.c_void_p(_stream_handle(stream))), "bf_apply")
+
+
+def bf_apply_adjoint(plan: Plan, x, y, nrhs: int | None = None, ld: int | None = None, stream=None) -> None:
+    """y = K_bf^* x (asynchronous on `stream`)."""
+    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
+    _check(load().bf_apply_adjoint(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi), n, l,
+                                   ctypes.c_void_p(_stream_handle(stream))), "bf_apply_adjoint")
+
+
+def bf_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def bf_plan_check(plan: Plan, stream=None) -> None:
+    """Raise BfError(BF_ERR_TIMEOUT) if a kernel gave up on a bounded wait."""
+    _check(load().bf_plan_check(ctypes.c_void_p(plan.handle), ctypes.c_void_p(_stream_handle(stream))),
+           "bf_plan_check")
+
+
+def bf_plan_device_bytes(plan: Plan) -> int:
+    return int(load().bf_plan_device_bytes(ctypes.c_void_p(plan.handle)))
+
+
+def bf_plan_set_profiling(plan: Plan, enable: bool) -> None:
+    _check(load().bf_plan_set_profiling(ctypes.c_void_p(plan.handle), 1 if enable else 0), "bf_plan_set_profiling")
+
+
+def bf_plan_kernel_times(plan: Plan) -> dict:
+    """{'down': (launches, ms), 'up': (launches, ms)} since the last call."""
+    dl, ul = ctypes.c_int(), ctypes.c_int()
+    dm, um = ctypes.c_double(), ctypes.c_double()
+    _check(load().bf_plan_kernel_times(ctypes.c_void_p(plan.handle), ctypes.byref(dl), ctypes.byref(dm),
+                                       ctypes.byref(ul), ctypes.byref(um)), "bf_plan_kernel_times")
+    return {"down": (dl.value, dm.value), "up": (ul.value, um.value)}

@@ -1,0 +1,500 @@
+// C ABI of the butterfly apply library: plan creation (validation, factor
+// packing, upload), apply / adjoint launches, profiling and error checks.
+// Declarations and argument documentation: include/bfly.h.
+#include "bfly.h"
+#include "bf_kernels.cuh"
+
+#include <algorithm>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+namespace {
+
+using bfk::Level;
+using bfk::Params;
+
+constexpr int kMaxSmem = 232448;  // 227 KB opt-in per block on sm_100/sm_103
+
+// One packed factor stream: the factors one kernel reads, chunked per CTA.
+struct Stream {
+    float2 *d = nullptr;
+    long long cta_len = 0;
+    int nlev = 0;
+    Level lev[bfk::kMaxLevels];
+};
+
+// Forward or adjoint direction: the down and up kernels' streams and the S rows.
+struct Direction {
+    Stream down, up;
+    float *d_S = nullptr;  // (node, q, k) weights for the up kernel's gather
+};
+
+struct Timing {
+    cudaEvent_t a, b, c;
+};
+
+}  // namespace
+
+struct bf_plan_s {
+    int L, n0, r, h, m, W, nrhs_max;
+    long long N, R;
+    int stages, slot_len, consumers;
+    Direction fwd, adj;
+    float2 *d_ws = nullptr;                       // R x nrhs_max level-h vectors
+    float2 *d_stage_in = nullptr, *d_stage_out = nullptr;  // host-pointer staging, N x nrhs_max
+    unsigned *d_err = nullptr;
+    size_t device_bytes = 0;
+    bool profiling = false;
+    std::vector<Timing> timings;
+    size_t timing_used = 0;
+};
+
+namespace {
+
+int env_int(const char *name, int dflt) {
+    const char *v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    char *end = nullptr;
+    long x = std::strtol(v, &end, 10);
+    return (end && *end == 0 && x > 0 && x < (1 << 30)) ? (int)x : dflt;
+}
+
+bf_status cuda_fail(cudaError_t e) {
+    (void)e;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
+}
+
+#define BF_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_);    \
+    } while (0)
+
+// Reads element (block, row, col) of a canonical row-major factor array.
+struct Src {
+    const void *p;
+    int dtype;
+    int rows, cols;
+    inline float2 at(long long blk, int row, int col) const {
+        const long long i = (blk * rows + row) * (long long)cols + col;
+        if (dtype == BF_C64) return static_cast<const float2 *>(p)[i];
+        const double2 v = static_cast<const double2 *>(p)[i];
+        return make_float2((float)v.x, (float)v.y);
+    }
+};
+
+inline float2 conjf2(float2 v) { return make_float2(v.x, -v.y); }
+
+// Level table of one stream.  Down: leaf then merging levels t = 1..h
+// (segments of s = 2^t blocks, i.e. factor level l = L - t).  Up: splitting
+// levels t = h..1 then the leaf.
+void make_levels(Stream &st, bool down, int h, int m, int n0, int r, int slot_len) {
+    auto fill = [&](Level &lv, int kind, int K, int rpu, int nunits, int s) {
+        int upb = 1;
+        while (upb * 2 <= nunits && (long long)(upb * 2) * K * rpu <= slot_len) upb *= 2;
+        lv.kind = kind;
+        lv.K = K;
+        lv.rpu = rpu;
+        lv.upb = upb;
+        lv.nstages = nunits / upb;
+        lv.stage_len = (upb * K * rpu + 1) & ~1;
+        lv.s = s;
+        lv.pad_ = 0;
+    };
+    int n = 0;
+    if (down) {
+        fill(st.lev[n++], bfk::LEAF_IN, n0, r, m, 1);
+        for (int t = 1; t <= h; ++t) fill(st.lev[n++], bfk::MERGE, 2 * r, 2 * r, m / 2, 1 << t);
+    } else {
+        for (int t = h; t >= 1; --t) fill(st.lev[n++], bfk::SPLIT, 2 * r, 2 * r, m / 2, 1 << t);
+        fill(st.lev[n++], bfk::LEAF_OUT, r, n0, m, 1);
+    }
+    st.nlev = n;
+    st.cta_len = 0;
+    for (int i = 0; i < n; ++i) st.cta_len += (long long)st.lev[i].nstages * st.lev[i].stage_len;
+}
+
+// Which factor a stream packs.
+enum StreamKind { FWD_DOWN, FWD_UP, ADJ_DOWN, ADJ_UP };
+
+// Packs one stream: for CTA (node) c, level by level, stage by stage, the
+// units' matrices B (rpu x K) stored k-major over the stage's rows:
+// dst[k * (upb*rpu) + u_in * rpu + rr] = B_u[rr][k].
+void pack_stream(float2 *dst, const Stream &st, StreamKind kind, const bf_plan_s &P, const bf_factors &f) {
+    const int L = P.L, h = P.h, m = P.m, n0 = P.n0, r = P.r;
+    const Src VL{f.VL, f.dtype, n0, r}, UL{f.UL, f.dtype, n0, r};
+    auto work = [&](int c0, int c1) {
+        for (int c = c0; c < c1; ++c) {
+            float2 *o = dst + (long long)c * st.cta_len;
+            for (int li = 0; li < st.nlev; ++li) {
+                const Level &lv = st.lev[li];
+                const int rows = lv.upb * lv.rpu;
+                for (int stg = 0; stg < lv.nstages; ++stg) {
+                    for (int ui = 0; ui < lv.upb; ++ui) {
+                        const int u = stg * lv.upb + ui;
+                        for (int rr = 0; rr < lv.rpu; ++rr) {
+                            for (int k = 0; k < lv.K; ++k) {
+                                float2 v;
+                                if (lv.kind == bfk::LEAF_IN || lv.kind == bfk::LEAF_OUT) {
+                                    const long long b = (long long)c * m + u;
+                                    const Src &S = (kind == FWD_DOWN || kind == ADJ_UP) ? VL : UL;
+                                    if (lv.kind == bfk::LEAF_IN) v = conjf2(S.at(b, k, rr));  // (X^L_b)^*: rr = col k, k = point p
+                                    else v = S.at(b, rr, k);                                   // X^L_b: rr = point p, k = col
+                                } else {
+                                    const int s = lv.s, hs = s >> 1;
+                                    const int l = L - __builtin_ctz(s);        // factor level
+                                    const int seg = u / hs, q = u % hs;
+                                    const long long nodel = (long long)c * (m / s) + seg;  // tree node at level l
+                                    const bool is_h = (kind == FWD_DOWN || kind == ADJ_UP);
+                                    const Src X{is_h ? f.H[l - h] : f.G[l - h], f.dtype, r, 2 * r};
+                                    if (lv.kind == bfk::MERGE) {
+                                        // rr = d*r + kk (output block 2q+d), k = c'*r + k' (input block c'*hs+q)
+                                        const int cc = k / r, kp = k % r;
+                                        const long long blk = (2 * nodel + cc) * hs + q;
+                                        // (X^l_{2n+c',q})^*: entry (d*r+kk, k') = conj(X[k'][d*r+kk])
+                                        v = conjf2(X.at(blk, kp, rr));
+                                    } else {
+                                        // rr = c'*r + kk (output block c'*hs+q), k = d*r + k' (input block 2q+d)
+                                        const int cc = rr / r, kk = rr % r;
+                                        const long long blk = (2 * nodel + cc) * hs + q;
+                                        v = X.at(blk, kk, k);
+                                    }
+                                }
+                                o[(long long)k * rows + (long long)ui * lv.rpu + rr] = v;
+                            }
+                        }
+                    }
+                    if (lv.stage_len > rows * lv.K) o[lv.stage_len - 1] = make_float2(0.f, 0.f);
+                    o += lv.stage_len;
+                }
+            }
+        }
+    };
+    int nthreads = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    nthreads = std::min(nthreads, m);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t) pool.emplace_back(work, (int)((long long)m * t / nthreads), (int)((long long)m * (t + 1) / nthreads));
+    for (auto &th : pool) th.join();
+}
+
+bf_status upload_stream(bf_plan_s &P, Stream &st, StreamKind kind, const bf_factors &f) {
+    const size_t n = (size_t)P.m * st.cta_len;
+    std::vector<float2> host;
+    try {
+        host.resize(n);
+    } catch (const std::bad_alloc &) {
+        return BF_ERR_NOMEM;
+    }
+    pack_stream(host.data(), st, kind, P, f);
+    BF_CUDA(cudaMalloc(&st.d, n * sizeof(float2)));
+    P.device_bytes += n * sizeof(float2);
+    BF_CUDA(cudaMemcpy(st.d, host.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    return BF_OK;
+}
+
+bf_status upload_S(bf_plan_s &P, const bf_factors &f) {
+    const int m = P.m, r = P.r;
+    const size_t n = (size_t)m * m * r;
+    std::vector<float> fw(n), ad(n);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j)
+            for (int k = 0; k < r; ++k) {
+                const size_t src = ((size_t)i * m + j) * r + k;
+                const float v = f.dtype == BF_C64 ? static_cast<const float *>(f.S)[src]
+                                                  : (float)static_cast<const double *>(f.S)[src];
+                fw[src] = v;                               // forward: row node i gathers q = j
+                ad[((size_t)j * m + i) * r + k] = v;       // adjoint: column node j gathers q = i
+            }
+    BF_CUDA(cudaMalloc(&P.fwd.d_S, n * sizeof(float)));
+    BF_CUDA(cudaMalloc(&P.adj.d_S, n * sizeof(float)));
+    P.device_bytes += 2 * n * sizeof(float);
+    BF_CUDA(cudaMemcpy(P.fwd.d_S, fw.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    BF_CUDA(cudaMemcpy(P.adj.d_S, ad.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    return BF_OK;
+}
+
+size_t plan_smem(const bf_plan_s &P, int T) { return bfk::smem_bytes(P.stages, P.slot_len, P.m, P.W, T); }
+
+template <int T>
+bf_status set_smem_attr(size_t bytes) {
+    BF_CUDA(cudaFuncSetAttribute(bfk::bf_down_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    BF_CUDA(cudaFuncSetAttribute(bfk::bf_up_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return BF_OK;
+}
+
+void free_plan(bf_plan_s *P) {
+    if (!P) return;
+    for (Direction *d : {&P->fwd, &P->adj}) {
+        cudaFree(d->down.d);
+        cudaFree(d->up.d);
+        cudaFree(d->d_S);
+    }
+    cudaFree(P->d_ws);
+    cudaFree(P->d_stage_in);
+    cudaFree(P->d_stage_out);
+    cudaFree(P->d_err);
+    for (auto &t : P->timings) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+        cudaEventDestroy(t.c);
+    }
+    cudaGetLastError();
+    delete P;
+}
+
+Params base_params(const bf_plan_s &P, const Stream &st) {
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.fac = st.d;
+    p.cta_len = st.cta_len;
+    p.err = P.d_err;
+    p.nlev = st.nlev;
+    for (int i = 0; i < st.nlev; ++i) p.lev[i] = st.lev[i];
+    p.m = P.m;
+    p.r = P.r;
+    p.n0 = P.n0;
+    p.W = P.W;
+    p.stages = P.stages;
+    p.slot_len = P.slot_len;
+    return p;
+}
+
+template <int T>
+cudaError_t launch_pair(const bf_plan_s &P, const Direction &D, const float2 *in, long long ld_in, float2 *out,
+                        long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
+    const dim3 grid((nrhs + T - 1) / T, P.m);
+    const dim3 block(P.consumers + 32);
+    const size_t smem = plan_smem(P, T);
+    Params pd = base_params(P, D.down);
+    pd.in = in;
+    pd.ld_in = ld_in;
+    pd.out = P.d_ws;
+    pd.ld_out = P.R;
+    pd.nrhs = nrhs;
+    Params pu = base_params(P, D.up);
+    pu.in = P.d_ws;
+    pu.ld_in = P.R;
+    pu.out = out;
+    pu.ld_out = ld_out;
+    pu.S = D.d_S;
+    pu.nrhs = nrhs;
+    if (tm) cudaEventRecord(tm->a, s);
+    bfk::bf_down_kernel<T><<<grid, block, smem, s>>>(pd);
+    if (tm) cudaEventRecord(tm->b, s);
+    bfk::bf_up_kernel<T><<<grid, block, smem, s>>>(pu);
+    if (tm) cudaEventRecord(tm->c, s);
+    return cudaGetLastError();
+}
+
+int pick_T(const bf_plan_s &P, int nrhs) {
+    int T = 1;
+    for (int cand : {2, 4})
+        if (nrhs >= cand && plan_smem(P, cand) <= (size_t)kMaxSmem) T = cand;
+    return T;
+}
+
+Timing *next_timing(bf_plan_s &P) {
+    if (!P.profiling) return nullptr;
+    if (P.timing_used == P.timings.size()) {
+        Timing t;
+        if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess ||
+            cudaEventCreate(&t.c) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        P.timings.push_back(t);
+    }
+    return &P.timings[P.timing_used++];
+}
+
+bool is_host_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cudaStream_t s, bool adjoint) {
+    if (!P || !in || !out || nrhs < 0 || ld < P->N) return BF_ERR_INVALID;
+    if (nrhs == 0) return BF_OK;
+    const char *ib = static_cast<const char *>(in);
+    const char *ob = static_cast<const char *>(out);
+    const long long span = ((long long)(nrhs - 1) * ld + P->N) * 8;
+    if (ib < ob + span && ob < ib + span) return BF_ERR_INVALID;
+    const Direction &D = adjoint ? P->adj : P->fwd;
+    const bool host_in = is_host_pointer(in), host_out = is_host_pointer(out);
+    if ((host_in || host_out) && !P->d_stage_in) {
+        const size_t bytes = (size_t)P->N * P->nrhs_max * sizeof(float2);
+        BF_CUDA(cudaMalloc(&P->d_stage_in, bytes));
+        BF_CUDA(cudaMalloc(&P->d_stage_out, bytes));
+        P->device_bytes += 2 * bytes;
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += P->nrhs_max) {
+        const int nc = std::min(P->nrhs_max, nrhs - c0);
+        const float2 *src = static_cast<const float2 *>(in) + (long long)c0 * ld;
+        float2 *dst = static_cast<float2 *>(out) + (long long)c0 * ld;
+        long long ld_in = ld, ld_out = ld;
+        if (host_in) {
+            BF_CUDA(cudaMemcpy2DAsync(P->d_stage_in, P->N * 8, src, ld * 8, P->N * 8, nc, cudaMemcpyHostToDevice, s));
+            src = P->d_stage_in;
+            ld_in = P->N;
+        }
+        float2 *kdst = host_out ? P->d_stage_out : dst;
+        if (host_out) ld_out = P->N;
+        const int T = pick_T(*P, nc);
+        Timing *tm = next_timing(*P);
+        cudaError_t e = T == 4 ? launch_pair<4>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm)
+                      : T == 2 ? launch_pair<2>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm)
+                               : launch_pair<1>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (host_out)
+            BF_CUDA(cudaMemcpy2DAsync(dst, ld * 8, P->d_stage_out, P->N * 8, P->N * 8, nc, cudaMemcpyDeviceToHost, s));
+    }
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f, cudaStream_t stream) {
+    if (!plan) return BF_ERR_INVALID;
+    *plan = nullptr;
+    if (!desc || !f) return BF_ERR_INVALID;
+    const int L = desc->L, n0 = desc->leaf, r = desc->r;
+    if (L < 0 || (L & 1) || n0 < 1 || r < 1 || desc->nrhs_max < 1) return BF_ERR_INVALID;
+    if (f->dtype != BF_C64 && f->dtype != BF_C128) return BF_ERR_INVALID;
+    if (!f->VL || !f->UL || !f->S) return BF_ERR_INVALID;
+    if (L > 0 && (!f->H || !f->G)) return BF_ERR_INVALID;
+    if (L > 24 || r > 32 || n0 > 64) return BF_ERR_UNSUPPORTED;
+    for (int t = 0; t < L / 2; ++t)
+        if (!f->H[t] || !f->G[t]) return BF_ERR_INVALID;
+    bf_plan_s *P = new (std::nothrow) bf_plan_s();
+    if (!P) return BF_ERR_NOMEM;
+    P->L = L;
+    P->n0 = n0;
+    P->r = r;
+    P->h = L / 2;
+    P->m = 1 << P->h;
+    P->W = std::max(n0, r);
+    P->nrhs_max = desc->nrhs_max;
+    P->N = (long long)n0 << L;
+    P->R = (1LL << L) * r;
+    if ((long long)P->m * P->W > 8192) {
+        delete P;
+        return BF_ERR_UNSUPPORTED;
+    }
+    // Ring: `stages` slots of `slot_len` complex entries; one slot must hold a
+    // whole 2r x 2r butterfly (4r^2) and a whole leaf (n0 r).
+    P->consumers = std::min(256, std::max(32, env_int("BF_CONSUMERS", 128) / 32 * 32));
+    int slot_len = env_int("BF_SLOT_KB", 32) * 128;
+    slot_len = std::max(slot_len, std::max(4 * r * r, n0 * r + 1));
+    P->slot_len = (slot_len + 1) & ~1;
+    P->stages = std::max(2, env_int("BF_STAGES", 4));
+    while (P->stages > 2 && plan_smem(*P, 1) > (size_t)kMaxSmem) --P->stages;
+    if (plan_smem(*P, 1) > (size_t)kMaxSmem) {
+        delete P;
+        return BF_ERR_UNSUPPORTED;
+    }
+    bf_status st = BF_OK;
+    auto fail = [&](bf_status e) {
+        free_plan(P);
+        return e;
+    };
+    if ((st = set_smem_attr<1>(plan_smem(*P, 1))) != BF_OK) return fail(st);
+    if (plan_smem(*P, 2) <= (size_t)kMaxSmem && (st = set_smem_attr<2>(plan_smem(*P, 2))) != BF_OK) return fail(st);
+    if (plan_smem(*P, 4) <= (size_t)kMaxSmem && (st = set_smem_attr<4>(plan_smem(*P, 4))) != BF_OK) return fail(st);
+    make_levels(P->fwd.down, true, P->h, P->m, n0, r, P->slot_len);
+    make_levels(P->fwd.up, false, P->h, P->m, n0, r, P->slot_len);
+    make_levels(P->adj.down, true, P->h, P->m, n0, r, P->slot_len);
+    make_levels(P->adj.up, false, P->h, P->m, n0, r, P->slot_len);
+    if ((st = upload_stream(*P, P->fwd.down, FWD_DOWN, *f)) != BF_OK) return fail(st);
+    if ((st = upload_stream(*P, P->fwd.up, FWD_UP, *f)) != BF_OK) return fail(st);
+    if ((st = upload_stream(*P, P->adj.down, ADJ_DOWN, *f)) != BF_OK) return fail(st);
+    if ((st = upload_stream(*P, P->adj.up, ADJ_UP, *f)) != BF_OK) return fail(st);
+    if ((st = upload_S(*P, *f)) != BF_OK) return fail(st);
+    const size_t ws = (size_t)P->R * P->nrhs_max * sizeof(float2);
+    if (cudaMalloc(&P->d_ws, ws) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
+    P->device_bytes += ws;
+    if (cudaMalloc(&P->d_err, sizeof(unsigned)) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
+    if (cudaMemsetAsync(P->d_err, 0, sizeof(unsigned), stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(cuda_fail(cudaErrorUnknown));
+    *plan = P;
+    return BF_OK;
+}
+
+bf_status bf_apply(bf_plan plan, const void *in, void *out, int nrhs, long long ld, cudaStream_t stream) {
+    return run(plan, in, out, nrhs, ld, stream, false);
+}
+
+bf_status bf_apply_adjoint(bf_plan plan, const void *in, void *out, int nrhs, long long ld, cudaStream_t stream) {
+    return run(plan, in, out, nrhs, ld, stream, true);
+}
+
+bf_status bf_plan_destroy(bf_plan plan) {
+    if (!plan) return BF_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return BF_OK;
+}
+
+bf_status bf_plan_check(bf_plan plan, cudaStream_t stream) {
+    if (!plan) return BF_ERR_INVALID;
+    unsigned h = 0;
+    BF_CUDA(cudaMemcpyAsync(&h, plan->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+    BF_CUDA(cudaStreamSynchronize(stream));
+    if (h) {
+        BF_CUDA(cudaMemsetAsync(plan->d_err, 0, sizeof(unsigned), stream));
+        BF_CUDA(cudaStreamSynchronize(stream));
+        return BF_ERR_TIMEOUT;
+    }
+    return BF_OK;
+}
+
+size_t bf_plan_device_bytes(bf_plan plan) { return plan ? plan->device_bytes : 0; }
+
+bf_status bf_plan_set_profiling(bf_plan plan, int enable) {
+    if (!plan) return BF_ERR_INVALID;
+    plan->profiling = enable != 0;
+    return BF_OK;
+}
+
+bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms, int *up_launches, double *up_ms) {
+    if (!plan || !down_launches || !down_ms || !up_launches || !up_ms) return BF_ERR_INVALID;
+    BF_CUDA(cudaDeviceSynchronize());
+    double d = 0, u = 0;
+    for (size_t i = 0; i < plan->timing_used; ++i) {
+        float a = 0, b = 0;
+        BF_CUDA(cudaEventElapsedTime(&a, plan->timings[i].a, plan->timings[i].b));
+        BF_CUDA(cudaEventElapsedTime(&b, plan->timings[i].b, plan->timings[i].c));
+        d += a;
+        u += b;
+    }
+    *down_launches = *up_launches = (int)plan->timing_used;
+    *down_ms = d;
+    *up_ms = u;
+    plan->timing_used = 0;
+    return BF_OK;
+}
+
+const char *bf_status_string(bf_status s) {
+    switch (s) {
+        case BF_OK: return "BF_OK";
+        case BF_ERR_INVALID: return "BF_ERR_INVALID: invalid argument";
+        case BF_ERR_CUDA: return "BF_ERR_CUDA: a CUDA runtime call failed";
+        case BF_ERR_NOMEM: return "BF_ERR_NOMEM: out of memory";
+        case BF_ERR_UNSUPPORTED: return "BF_ERR_UNSUPPORTED: shape outside this build's limits";
+        case BF_ERR_TIMEOUT: return "BF_ERR_TIMEOUT: a kernel wait expired";
+    }
+    return "unknown bf_status";
+}
+
+}  // extern "C"

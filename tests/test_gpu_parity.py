@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA apply/adjoint (through the C ABI) against the FP64 oracle
+apply of the same factors, element by element.
+
+Tolerance: relative 2-norm error <= 1e-5 over all entries (FP32 arithmetic;
+each output is a chain of L+3 sparse products, each summing at most 2r or n0
+products, so the expected error is a few 1e-7).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_01379_gb300 import build as pkg_build
+    pkg_build.build()
+    import paper_1502_01379_gb300 as mod
+    mod.load()
+    torch.cuda.set_device(0)
+    return mod
+
+
+def _oracle(F, x, adjoint=False):
+    from oracle import apply as A
+    F64 = F.astype(np.complex128)
+    fn = A.bf_adjoint if adjoint else A.bf_apply
+    return fn(F64, np.asarray(x).T.astype(np.complex128)).T
+
+
+def _rel(a, b):
+    from oracle.kernel import rel_err
+    return rel_err(a, b)
+
+
+def _run(bf, plan, x_np, adjoint=False, ld=None):
+    dev = torch.device("cuda:0")
+    nrhs, N = x_np.shape
+    if ld is None:
+        x = torch.from_numpy(x_np).to(dev)
+        y = torch.empty_like(x)
+        (bf.bf_apply_adjoint if adjoint else bf.bf_apply)(plan, x, y)
+        torch.cuda.synchronize()
+        bf.bf_plan_check(plan)
+        return y.cpu().numpy()
+    xp = torch.zeros((nrhs, ld), dtype=torch.complex64, device=dev)
+    xp[:, :N] = torch.from_numpy(x_np).to(dev)
+    yp = torch.full((nrhs, ld), 7.0 + 7.0j, dtype=torch.complex64, device=dev)
+    (bf.bf_apply_adjoint if adjoint else bf.bf_apply)(plan, xp, yp, nrhs=nrhs, ld=ld)
+    torch.cuda.synchronize()
+    bf.bf_plan_check(plan)
+    out = yp.cpu().numpy()
+    assert np.all(out[:, N:] == 7.0 + 7.0j), "padding between columns was written"
+    return out[:, :N]
+
+
+SHAPES = [  # (L, n0, r): degenerate L = 0, tiny trees, odd n0*r, r = 1, r = 32, n0 = 64
+    (0, 5, 3), (0, 1, 1), (2, 2, 3), (2, 1, 1), (4, 3, 5), (4, 16, 32), (6, 1, 1), (6, 16, 12),
+    (8, 16, 12), (8, 64, 4), (10, 16, 16), (12, 2, 7),
+]
+
+
+@pytest.mark.parametrize("L,n0,r", SHAPES)
+def test_synthetic_shapes_apply_and_adjoint(bf, L, n0, r):
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(L, n0, r, seed=100 + L + r, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=4)
+    for nrhs in (1, 3):
+        g = complex_normal((nrhs, F.N), seed=nrhs, dtype=np.complex64)
+        assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+        assert _rel(_run(bf, plan, g, adjoint=True), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
+def test_fio_n4096_r12_against_oracle(bf):
+    """1D FIO of Example 1, N = 4096, L = 8 (leaf 16), r = 12, factors built by
+    the oracle's entry-sampling construction in FP64, one RHS (seed 0)."""
+    from bfinputs import complex_normal
+    from oracle import construct
+    F = construct.construct(4096, 8, 12, "fio", seed=0).astype(np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    g = complex_normal((1, F.N), seed=0, dtype=np.complex64)
+    assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+    assert _rel(_run(bf, plan, g, adjoint=True), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
+def test_dft_against_fft_closed_form(bf):
+    """Fourier matrix (Sec. 1.1): the GPU apply of the oracle's factorization
+    reproduces (-1)^j N ifft(g) within the construction's eps + FP32 rounding."""
+    from bfinputs import complex_normal
+    from oracle import construct
+    from oracle import kernel as K
+    N = 1024
+    F64 = construct.construct(N, 10, 10, "dft", seed=0)
+    plan = bf.bf_plan_create(F64.astype(np.complex64), nrhs_max=2)
+    g = complex_normal((2, N), seed=3, dtype=np.complex64)
+    u = _run(bf, plan, g)
+    ref = K.dft_closed_form(g.T.astype(np.complex128), N).T
+    assert _rel(u, ref) < max(TOL, 10 * F64.meta["eps"])
+    plan.destroy()
+
+
+def test_batches_ragged_tiles_chunks_and_ld(bf):
+    """nrhs above nrhs_max (several passes), ragged RHS tiles, ld > N."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(8, 4, 6, seed=5, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=3)
+    for nrhs in (1, 2, 5, 7):
+        g = complex_normal((nrhs, F.N), seed=40 + nrhs, dtype=np.complex64)
+        assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+        assert _rel(_run(bf, plan, g, adjoint=True, ld=F.N + 24), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
+def test_complex128_factor_input(bf):
+    """Factors given in complex128 are rounded to complex64 on upload."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(6, 4, 5, seed=8, dtype=np.complex128)
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    g = complex_normal((1, F.N), seed=9, dtype=np.complex64)
+    assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+    plan.destroy()
+
+
+def test_host_buffers_pinned_and_pageable(bf):
+    """bf_apply with host pointers stages through device buffers."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(6, 8, 6, seed=21, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=2)
+    g = complex_normal((3, F.N), seed=22, dtype=np.complex64)
+    # pageable numpy buffers
+    out = np.zeros_like(g)
+    bf.bf_apply(plan, g, out, nrhs=3)
+    torch.cuda.synchronize()
+    assert _rel(out, _oracle(F, g)) < TOL
+    # pinned torch buffers
+    gp = torch.from_numpy(g).pin_memory()
+    op = torch.zeros_like(gp).pin_memory()
+    bf.bf_apply_adjoint(plan, gp, op, nrhs=3)
+    torch.cuda.synchronize()
+    assert _rel(op.numpy(), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
+def test_adjoint_identity_fp32(bf):
+    """<K g, f> = <g, K^* f> for the GPU apply and adjoint (FP32)."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(10, 16, 8, seed=2, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    g = complex_normal((1, F.N), seed=1, dtype=np.complex64)
+    f = complex_normal((1, F.N), seed=2, dtype=np.complex64)
+    Kg = _run(bf, plan, g).astype(np.complex128)
+    Kf = _run(bf, plan, f, adjoint=True).astype(np.complex128)
+    lhs = np.vdot(f, Kg)
+    rhs = np.vdot(Kf, g)
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(Kg) * np.linalg.norm(f)
+    plan.destroy()
+
+
+def test_zero_rhs_and_invalid_calls(bf):
+    from bfinputs import synthetic_factors
+    F = synthetic_factors(4, 4, 4, seed=1, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    x = torch.zeros((2, F.N), dtype=torch.complex64, device="cuda")
+    bf.bf_apply(plan, x, x[1:], nrhs=0)                     # no-op
+    with pytest.raises(bf.BfError) as e:
+        bf.bf_apply(plan, x, x, nrhs=1)                     # in == out
+    assert e.value.status == bf.BF_ERR_INVALID
+    with pytest.raises(bf.BfError) as e:
+        bf.bf_apply(plan, x, x[1:], nrhs=1, ld=F.N - 1)     # ld < N
+    assert e.value.status == bf.BF_ERR_INVALID
+    assert bf.bf_plan_device_bytes(plan) > 0
+    plan.destroy()
+
+
+def test_profiling_counts_launches(bf):
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(6, 4, 4, seed=1, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    bf.bf_plan_set_profiling(plan, True)
+    g = torch.from_numpy(complex_normal((1, F.N), seed=1, dtype=np.complex64)).cuda()
+    y = torch.empty_like(g)
+    for _ in range(3):
+        bf.bf_apply(plan, g, y)
+    t = bf.bf_plan_kernel_times(plan)
+    assert t["down"][0] == 3 and t["up"][0] == 3 and t["down"][1] > 0 and t["up"][1] > 0
+    plan.destroy()
+
+
+@pytest.mark.slow
+def test_full_size_n1m_r16_against_c_oracle(bf):
+    """N = 2^20, L = 16 (leaf 16), r = 16 -- the benchmarked shape -- in the
+    launch configuration the benchmark times (one RHS), every output entry
+    against the FP64 C loops of the oracle on the same factors."""
+    from bfinputs import complex_normal, synthetic_factors
+    from oracle import capply
+    F = synthetic_factors(16, 16, 16, seed=0, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    g = complex_normal((1, F.N), seed=0, dtype=np.complex64)
+    P = capply.PreparedFactors(F)
+    u = _run(bf, plan, g)
+    assert _rel(u[0], capply.bf_apply_c(P, g[0])) < TOL
+    a = _run(bf, plan, g, adjoint=True)
+    assert _rel(a[0], capply.bf_adjoint_c(P, g[0])) < TOL
+    plan.destroy()
