@@ -393,11 +393,13 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
     }
     // Ring: `stages` slots of `slot_len` complex entries; one slot must hold a
     // whole 2r x 2r butterfly (4r^2) and a whole leaf (n0 r).
-    P->consumers = std::min(256, std::max(32, env_int("BF_CONSUMERS", 128) / 32 * 32));
-    int slot_len = env_int("BF_SLOT_KB", 32) * 128;
+    // Defaults measured on GB300 at N = 2^20, r = 16: 256 consumers, 64 KB
+    // slots and as many slots as fit (2 there) stream at the HBM copy rate.
+    P->consumers = std::min(256, std::max(32, env_int("BF_CONSUMERS", 256) / 32 * 32));
+    int slot_len = env_int("BF_SLOT_KB", 64) * 128;
     slot_len = std::max(slot_len, std::max(4 * r * r, n0 * r + 1));
     P->slot_len = (slot_len + 1) & ~1;
-    P->stages = std::max(2, env_int("BF_STAGES", 4));
+    P->stages = std::max(2, env_int("BF_STAGES", 3));
     while (P->stages > 2 && plan_smem(*P, 1) > (size_t)kMaxSmem) --P->stages;
     if (plan_smem(*P, 1) > (size_t)kMaxSmem) {
         delete P;

@@ -133,13 +133,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
 }
 
-__device__ __forceinline__ void cfma(float2 &acc, float2 f, float2 x) {
-    acc.x = fmaf(f.x, x.x, acc.x);
-    acc.x = fmaf(-f.y, x.y, acc.x);
-    acc.y = fmaf(f.x, x.y, acc.y);
-    acc.y = fmaf(f.y, x.x, acc.y);
-}
-
 // --------------------------------------------------------------- producer
 // One thread streams this CTA's factor chunk, stage by stage, into the ring.
 __device__ __forceinline__ void produce(const Params &p, float2 *ring, uint64_t *full, uint64_t *empty,
@@ -180,25 +173,66 @@ __device__ __forceinline__ void produce(const Params &p, float2 *ring, uint64_t 
 }
 
 // ------------------------------------------------------- consumer: one stage
-// Output rows `row` of the stage's units: acc[t] = sum_k F[k][row] * x_t[k],
-// with x[k] taken from xa for k < half and from xb above.
+// One complex output for T right-hand sides, kept as four independent FMA
+// chains (re*re, im*im, re*im, im*re) so consecutive k do not serialize.
 template <int T>
-__device__ __forceinline__ void stage_dot(const float2 *__restrict__ stg, int rows, int row, int K,
-                                          const float2 *xa, const float2 *xb, int half, float2 (&acc)[T]) {
+struct Acc {
+    float rr[T], ii[T], ri[T], ir[T];
+    __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int t = 0; t < T; ++t) acc[t] = make_float2(0.f, 0.f);
-    const float2 *f = stg + row;
-#pragma unroll 4
-    for (int k = 0; k < half; ++k) {
-        const float2 fk = f[(long long)k * rows];
-#pragma unroll
-        for (int t = 0; t < T; ++t) cfma(acc[t], fk, xa[k * T + t]);
+        for (int t = 0; t < T; ++t) rr[t] = ii[t] = ri[t] = ir[t] = 0.f;
     }
-#pragma unroll 4
-    for (int k = half; k < K; ++k) {
-        const float2 fk = f[(long long)k * rows];
+    __device__ __forceinline__ void mac(int t, float2 f, float2 x) {
+        rr[t] = fmaf(f.x, x.x, rr[t]);
+        ii[t] = fmaf(f.y, x.y, ii[t]);
+        ri[t] = fmaf(f.x, x.y, ri[t]);
+        ir[t] = fmaf(f.y, x.x, ir[t]);
+    }
+    __device__ __forceinline__ float2 get(int t) const { return make_float2(rr[t] - ii[t], ri[t] + ir[t]); }
+};
+
+// Rows r0 (and r0 + 1 when kPair) of a stage: a[t] = sum_k F[k][row] x_t[k],
+// x[k] from xa for k < half and from xb above.  In pair mode both rows belong
+// to the same unit, share x, and their factors arrive in one 16-byte load.
+template <int T, bool kPair>
+__device__ __forceinline__ void stage_dot(const float2 *__restrict__ stg, int rows, int r0, int K,
+                                          const float2 *xa, const float2 *xb, int half, Acc<T> &a0, Acc<T> &a1) {
+    a0.zero();
+    if (kPair) a1.zero();
+    const float2 *f = stg + r0;
+#pragma unroll 8
+    for (int k = 0; k < half; ++k) {
+        float2 f0, f1;
+        if (kPair) {
+            const float4 v = *reinterpret_cast<const float4 *>(f + k * rows);
+            f0 = make_float2(v.x, v.y);
+            f1 = make_float2(v.z, v.w);
+        } else {
+            f0 = f[k * rows];
+        }
 #pragma unroll
-        for (int t = 0; t < T; ++t) cfma(acc[t], fk, xb[(k - half) * T + t]);
+        for (int t = 0; t < T; ++t) {
+            const float2 x = xa[k * T + t];
+            a0.mac(t, f0, x);
+            if (kPair) a1.mac(t, f1, x);
+        }
+    }
+#pragma unroll 8
+    for (int k = half; k < K; ++k) {
+        float2 f0, f1;
+        if (kPair) {
+            const float4 v = *reinterpret_cast<const float4 *>(f + k * rows);
+            f0 = make_float2(v.x, v.y);
+            f1 = make_float2(v.z, v.w);
+        } else {
+            f0 = f[k * rows];
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const float2 x = xb[(k - half) * T + t];
+            a0.mac(t, f0, x);
+            if (kPair) a1.mac(t, f1, x);
+        }
     }
 }
 
@@ -237,63 +271,125 @@ __device__ __forceinline__ void setup(const Params &p, const Smem &s, int nconsu
     __syncthreads();
 }
 
-// Runs the levels [0, nlev) of this CTA on the segment buffers; returns the
-// buffer that holds the last level's output.
-template <int T, bool kDown>
-__device__ __forceinline__ float2 *run_levels(const Params &p, const Smem &s, int nconsumers, int rhs0,
-                                              int nt) {
+// Output position (in r-blocks * r + row, without the RHS interleave) of row
+// rr of unit u at a level of kind KIND, and the unit's input pointers.
+template <int T, int KIND>
+__device__ __forceinline__ void unit_io(const Params &p, const Level &lv, int lg_hs, float2 *xin, int u,
+                                        const float2 *&xa, const float2 *&xb, int &half, long long &obase) {
+    if (KIND == LEAF_IN) {
+        xa = xin + (long long)u * p.n0 * T;
+        xb = xa;
+        half = lv.K;
+        obase = (long long)u * p.r;
+    } else if (KIND == MERGE) {
+        // inputs: blocks seg*s + c*s/2 + q (c = 0, 1); outputs seg*s + 2q + d
+        const int hs = lv.s >> 1, seg = u >> lg_hs, q = u & (hs - 1);
+        const long long b0 = (long long)seg * lv.s + q;
+        xa = xin + b0 * p.r * T;
+        xb = xin + (b0 + hs) * p.r * T;
+        half = p.r;
+        obase = ((long long)seg * lv.s + 2 * q) * p.r;
+    } else if (KIND == SPLIT) {
+        // inputs: blocks seg*s + 2q + d; outputs seg*s + c*s/2 + q
+        const int hs = lv.s >> 1, seg = u >> lg_hs, q = u & (hs - 1);
+        xa = xin + ((long long)seg * lv.s + 2 * q) * p.r * T;
+        xb = xa;
+        half = lv.K;
+        obase = ((long long)seg * lv.s + q) * p.r;   // + c*hs*r + kk per row
+    } else {  // LEAF_OUT
+        xa = xin + (long long)u * p.r * T;
+        xb = xa;
+        half = lv.K;
+        obase = (long long)u * p.n0;
+    }
+}
+
+template <int T, int KIND>
+__device__ __forceinline__ void store_row(const Params &p, const Level &lv, float2 *xout, long long obase, int rr,
+                                          const Acc<T> &a, int node, int rhs0, int nt) {
+    if (KIND == LEAF_IN || KIND == MERGE) {
+#pragma unroll
+        for (int t = 0; t < T; ++t) xout[(obase + rr) * T + t] = a.get(t);
+    } else if (KIND == SPLIT) {
+        const int c = rr >= p.r ? 1 : 0;
+        const long long o = obase + (long long)c * (lv.s >> 1) * p.r + (rr - c * p.r);
+#pragma unroll
+        for (int t = 0; t < T; ++t) xout[o * T + t] = a.get(t);
+    } else {
+        const long long o = (long long)node * p.n0 * p.m + obase + rr;
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (t < nt) p.out[(long long)(rhs0 + t) * p.ld_out + o] = a.get(t);
+    }
+}
+
+// All stages of one level.  Work items are single rows, or pairs of
+// adjacent rows of one unit when the unit's row count is even.
+template <int T, int KIND>
+__device__ __forceinline__ void run_level(const Params &p, const Smem &s, const Level &lv, float2 *xin,
+                                          float2 *xout, uint32_t &gs, int nconsumers, int rhs0, int nt) {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int node = blockIdx.y;
+    const int rows = lv.upb * lv.rpu;
+    const bool pair = (lv.rpu & 1) == 0;
+    const int nitems = pair ? rows >> 1 : rows;
+    const int lg_hs = lv.s > 1 ? __ffs(lv.s >> 1) - 1 : 0;
+    // The first item of this thread has the same (unit-in-stage, row) in every stage.
+    const int r_first = pair ? 2 * tid : tid;
+    const int ui_first = r_first / lv.rpu;
+    const int rr_first = r_first - ui_first * lv.rpu;
+    for (int st = 0; st < lv.nstages; ++st, ++gs) {
+        const uint32_t slot = gs % p.stages;
+        const uint32_t use = gs / p.stages;
+        const bool ready = !*s.abort_flag && mbar_wait(&s.full[slot], use & 1, s.abort_flag, p.err);
+        if (ready) {
+            const float2 *stg = s.ring + (long long)slot * p.slot_len;
+            for (int it = tid; it < nitems; it += nconsumers) {
+                int r0, ui, rr;
+                if (it == tid) {
+                    r0 = r_first;
+                    ui = ui_first;
+                    rr = rr_first;
+                } else {
+                    r0 = pair ? 2 * it : it;
+                    ui = r0 / lv.rpu;
+                    rr = r0 - ui * lv.rpu;
+                }
+                const int u = st * lv.upb + ui;
+                const float2 *xa, *xb;
+                int half;
+                long long obase;
+                unit_io<T, KIND>(p, lv, lg_hs, xin, u, xa, xb, half, obase);
+                Acc<T> a0, a1;
+                if (pair) {
+                    stage_dot<T, true>(stg, rows, r0, lv.K, xa, xb, half, a0, a1);
+                    store_row<T, KIND>(p, lv, xout, obase, rr, a0, node, rhs0, nt);
+                    store_row<T, KIND>(p, lv, xout, obase, rr + 1, a1, node, rhs0, nt);
+                } else {
+                    stage_dot<T, false>(stg, rows, r0, lv.K, xa, xb, half, a0, a1);
+                    store_row<T, KIND>(p, lv, xout, obase, rr, a0, node, rhs0, nt);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s.empty[slot]);
+    }
+}
+
+// Runs the levels [0, nlev) of this CTA on the segment buffers; returns the
+// buffer that holds the last level's output.
+template <int T>
+__device__ __forceinline__ float2 *run_levels(const Params &p, const Smem &s, int nconsumers, int rhs0, int nt) {
     float2 *xin = s.buf0, *xout = s.buf1;
     uint32_t gs = 0;
     for (int l = 0; l < p.nlev; ++l) {
         const Level lv = p.lev[l];
-        const int rows = lv.upb * lv.rpu;
-        for (int st = 0; st < lv.nstages; ++st, ++gs) {
-            const uint32_t slot = gs % p.stages;
-            const uint32_t use = gs / p.stages;
-            const bool ready = !*s.abort_flag && mbar_wait(&s.full[slot], use & 1, s.abort_flag, p.err);
-            if (ready) {
-                const float2 *stg = s.ring + (long long)slot * p.slot_len;
-                for (int row = tid; row < rows; row += nconsumers) {
-                    const int u = st * lv.upb + row / lv.rpu;
-                    const int rr = row % lv.rpu;
-                    float2 acc[T];
-                    if (lv.kind == LEAF_IN) {
-                        // unit = leaf u of this node, output r-block u
-                        stage_dot<T>(stg, rows, row, lv.K, xin + (long long)u * p.n0 * T, nullptr, lv.K, acc);
-#pragma unroll
-                        for (int t = 0; t < T; ++t) xout[((long long)u * p.r + rr) * T + t] = acc[t];
-                    } else if (lv.kind == MERGE) {
-                        // inputs: blocks seg*s + c*s/2 + q (c = 0, 1); outputs seg*s + 2q + d
-                        const int hs = lv.s >> 1, seg = u / hs, q = u - seg * hs;
-                        const long long b0 = (long long)seg * lv.s + q;
-                        stage_dot<T>(stg, rows, row, lv.K, xin + b0 * p.r * T, xin + (b0 + hs) * p.r * T, p.r,
-                                     acc);
-                        const long long o = ((long long)seg * lv.s + 2 * q) * p.r + rr;
-#pragma unroll
-                        for (int t = 0; t < T; ++t) xout[o * T + t] = acc[t];
-                    } else if (lv.kind == SPLIT) {
-                        // inputs: blocks seg*s + 2q + d; outputs seg*s + c*s/2 + q
-                        const int hs = lv.s >> 1, seg = u / hs, q = u - seg * hs;
-                        const long long b0 = (long long)seg * lv.s + 2 * q;
-                        stage_dot<T>(stg, rows, row, lv.K, xin + b0 * p.r * T, nullptr, lv.K, acc);
-                        const int c = rr / p.r, kk = rr - c * p.r;
-                        const long long o = ((long long)seg * lv.s + c * hs + q) * p.r + kk;
-#pragma unroll
-                        for (int t = 0; t < T; ++t) xout[o * T + t] = acc[t];
-                    } else {  // LEAF_OUT: unit = leaf u of this node, n0 outputs to global
-                        stage_dot<T>(stg, rows, row, lv.K, xin + (long long)u * p.r * T, nullptr, lv.K, acc);
-                        const long long o = (long long)node * p.n0 * p.m + (long long)u * p.n0 + rr;
-#pragma unroll
-                        for (int t = 0; t < T; ++t)
-                            if (t < nt) p.out[(long long)(rhs0 + t) * p.ld_out + o] = acc[t];
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s.empty[slot]);
+        switch (lv.kind) {
+            case LEAF_IN: run_level<T, LEAF_IN>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
+            case MERGE: run_level<T, MERGE>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
+            case SPLIT: run_level<T, SPLIT>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
+            default: run_level<T, LEAF_OUT>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
         }
         consumer_sync(nconsumers);
         float2 *tmp = xin;
@@ -325,7 +421,7 @@ __global__ void __launch_bounds__(288, 1) bf_down_kernel(const Params p) {
             s.buf0[e] = (t < nt) ? __ldg(p.in + (long long)(rhs0 + t) * p.ld_in + base + ee) : make_float2(0.f, 0.f);
         }
         consumer_sync(nconsumers);
-        const float2 *res = run_levels<T, true>(p, s, nconsumers, rhs0, nt);
+        const float2 *res = run_levels<T>(p, s, nconsumers, rhs0, nt);
         // Segment `node` of the level-h vector: m*r consecutive entries per RHS.
         const int nseg = p.m * p.r;
         const long long obase = (long long)node * nseg;
@@ -364,7 +460,7 @@ __global__ void __launch_bounds__(288, 1) bf_up_kernel(const Params p) {
             s.buf0[e] = v;
         }
         consumer_sync(nconsumers);
-        run_levels<T, false>(p, s, nconsumers, rhs0, nt);
+        run_levels<T>(p, s, nconsumers, rhs0, nt);
     }
     __syncthreads();
 }
