@@ -123,6 +123,31 @@ bf_status bf_plan_set_profiling(bf_plan plan, int enable);
 bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms,
                                int *up_launches, double *up_ms);
 
+/* Apply without any device allocation: u = K_bf g (adjoint = 0) or
+ * K_bf^* g (adjoint != 0) like bf_apply / bf_apply_adjoint, but the level-h
+ * intermediate vector is kept in a fixed array of 2^21 complex64 entries
+ * (16 MiB) compiled into the library instead of the plan's workspace, and
+ * nothing is allocated, not even host-pointer staging.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc when they
+ * apply the operator -- code whose device memory is owned by another
+ * allocator (a framework's caching pool that has reserved the GPU), or
+ * latency-critical loops where an allocation and the device synchronization
+ * it implies are not acceptable.  The plan is still created once beforehand.
+ *   in, out  DEVICE pointers only (host pointers: BF_ERR_INVALID); same layout,
+ *            ld and aliasing rules as bf_apply.
+ *   Limit    2^L * r (one vector's level-h data) must be <= 2^21, else
+ *            BF_ERR_UNSUPPORTED; larger batches run in passes of
+ *            floor(2^21 / (2^L r)) vectors.
+ * Every GPU that loads the library holds the 16 MiB array until the process
+ * exits.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  All calls share the one array, which
+ * keeps the last call's contents (each pass overwrites what it reads, so
+ * nothing needs clearing): calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race and give wrong results. */
+bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int nrhs, long long ld,
+                                  int adjoint, cudaStream_t stream);
+
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);
 

@@ -20,7 +20,8 @@ BF_OK, BF_ERR_INVALID, BF_ERR_CUDA, BF_ERR_NOMEM, BF_ERR_UNSUPPORTED, BF_ERR_TIM
 BF_C64, BF_C128 = 1, 2
 
 EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", "bf_plan_check",
-           "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string")
+           "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string",
+           "bf_apply_static_scratch")
 
 
 class BfError(RuntimeError):
@@ -66,6 +67,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "bf_plan_kernel_times": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
         "bf_status_string": (ctypes.c_char_p, [i]),
+        "bf_apply_static_scratch": (i, [vp, vp, vp, i, ll, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -190,3 +192,14 @@ def bf_plan_kernel_times(plan: Plan) -> dict:
     _check(load().bf_plan_kernel_times(ctypes.c_void_p(plan.handle), ctypes.byref(dl), ctypes.byref(dm),
                                        ctypes.byref(ul), ctypes.byref(um)), "bf_plan_kernel_times")
     return {"down": (dl.value, dm.value), "up": (ul.value, um.value)}
+
+
+def bf_apply_static_scratch(plan: Plan, x, y, nrhs: int | None = None, ld: int | None = None,
+                            adjoint: bool = False, stream=None) -> None:
+    """y = K_bf x (or K_bf^* x) without any device allocation: the
+    intermediate vector lives in the library's fixed 16 MiB device array.
+    Device tensors only; calls that overlap on the GPU race."""
+    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
+    _check(load().bf_apply_static_scratch(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi),
+                                          n, l, 1 if adjoint else 0, ctypes.c_void_p(_stream_handle(stream))),
+           "bf_apply_static_scratch")

@@ -8,6 +8,7 @@
 #include <complex>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -360,6 +361,58 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
     return BF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Static scratch for bf_apply_static_scratch: the level-h vector lives in this
+// file-scope device array instead of a cudaMalloc'd workspace.  Every GPU that
+// loads the library holds it (16 MiB) until the process exits.
+constexpr long long kStaticScratchEntries = 1LL << 21;   // complex64 entries
+static __device__ __align__(256) float2 bf_static_scratch[kStaticScratchEntries];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_address[kMaxDevices] = {};
+
+// Device address of bf_static_scratch on the current device.  The host-side
+// name of the array is only a stand-in; the address is looked up once per
+// device (with that device current) and cached.
+bf_status static_scratch_address(float2 **out) {
+    int dev = 0;
+    BF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return BF_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_address[dev]) {
+        void *p = nullptr;
+        BF_CUDA(cudaGetSymbolAddress(&p, bf_static_scratch));
+        g_scratch_address[dev] = p;
+    }
+    *out = static_cast<float2 *>(g_scratch_address[dev]);
+    return BF_OK;
+}
+
+template <int T>
+cudaError_t launch_pair_static(const bf_plan_s &P, const Direction &D, const float2 *in, long long ld_in,
+                               float2 *out, long long ld_out, int nrhs, float2 *ws, cudaStream_t s) {
+    const dim3 grid((nrhs + T - 1) / T, P.m);
+    const dim3 block(P.consumers + 32);
+    const size_t smem = plan_smem(P, T);
+    Params pd = base_params(P, D.down);
+    pd.in = in;
+    pd.ld_in = ld_in;
+    pd.out = ws;
+    pd.ld_out = P.R;
+    pd.nrhs = nrhs;
+    Params pu = base_params(P, D.up);
+    pu.in = ws;
+    pu.ld_in = P.R;
+    pu.out = out;
+    pu.ld_out = ld_out;
+    pu.S = D.d_S;
+    pu.nrhs = nrhs;
+    bfk::bf_down_kernel<T><<<grid, block, smem, s>>>(pd);
+    bfk::bf_up_kernel<T><<<grid, block, smem, s>>>(pu);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -484,6 +537,35 @@ bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms
     *down_ms = d;
     *up_ms = u;
     plan->timing_used = 0;
+    return BF_OK;
+}
+
+bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int nrhs, long long ld, int adjoint,
+                                  cudaStream_t stream) {
+    bf_plan P = plan;
+    if (!P || !in || !out || nrhs < 0 || ld < P->N) return BF_ERR_INVALID;
+    if (P->R > kStaticScratchEntries) return BF_ERR_UNSUPPORTED;   // one vector's level-h data must fit
+    if (nrhs == 0) return BF_OK;
+    const char *ib = static_cast<const char *>(in);
+    const char *ob = static_cast<const char *>(out);
+    const long long span = ((long long)(nrhs - 1) * ld + P->N) * 8;
+    if (ib < ob + span && ob < ib + span) return BF_ERR_INVALID;
+    if (is_host_pointer(in) || is_host_pointer(out)) return BF_ERR_INVALID;   // staging would allocate
+    float2 *ws = nullptr;
+    bf_status st = static_scratch_address(&ws);
+    if (st != BF_OK) return st;
+    const Direction &D = adjoint ? P->adj : P->fwd;
+    const int per_pass = (int)std::min<long long>(kStaticScratchEntries / P->R, 1 << 30);
+    for (int c0 = 0; c0 < nrhs; c0 += per_pass) {
+        const int nc = std::min(per_pass, nrhs - c0);
+        const float2 *src = static_cast<const float2 *>(in) + (long long)c0 * ld;
+        float2 *dst = static_cast<float2 *>(out) + (long long)c0 * ld;
+        const int T = pick_T(*P, nc);
+        cudaError_t e = T == 4 ? launch_pair_static<4>(*P, D, src, ld, dst, ld, nc, ws, stream)
+                      : T == 2 ? launch_pair_static<2>(*P, D, src, ld, dst, ld, nc, ws, stream)
+                               : launch_pair_static<1>(*P, D, src, ld, dst, ld, nc, ws, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     return BF_OK;
 }
 
