@@ -3,6 +3,7 @@
 // Declarations and argument documentation: include/bfly.h.
 #include "bfly.h"
 #include "bf_kernels.cuh"
+#include "bf_wide.cuh"
 
 #include <algorithm>
 #include <complex>
@@ -38,6 +39,18 @@ struct Timing {
     cudaEvent_t a, b, c;
 };
 
+// One pass of the multi-RHS path (bf_wide.cuh): its packed stream and group geometry.
+struct WidePass {
+    Stream st;
+    int load_kind = 0, store_kind = 0;
+    int G = 1, gstride = 1, gmul = 1, ngroups = 1;
+};
+
+// D1, D2 (down half) and U1, U2 (up half) of one direction.
+struct WideDirection {
+    WidePass pass[4];
+};
+
 }  // namespace
 
 struct bf_plan_s {
@@ -52,6 +65,11 @@ struct bf_plan_s {
     bool profiling = false;
     std::vector<Timing> timings;
     size_t timing_used = 0;
+    // multi-RHS path
+    bool wide = false;
+    int wide_min = 0, wide_nr_max = 0, wide_stages = 0, wide_slot_len = 0, k1 = 0;
+    WideDirection wfwd, wadj;
+    float2 *d_wsA = nullptr;                       // R x nrhs_max pass intermediate
 };
 
 namespace {
@@ -219,6 +237,211 @@ bf_status upload_S(bf_plan_s &P, const bf_factors &f) {
     return BF_OK;
 }
 
+// ------------------------------------------------------------ multi-RHS path
+inline int host_insert0(int v, int b) { return ((v >> b) << (b + 1)) | (v & ((1 << b) - 1)); }
+inline int host_bitrev(int x, int bits) {
+    int y = 0;
+    for (int i = 0; i < bits; ++i) y |= ((x >> i) & 1) << (bits - 1 - i);
+    return y;
+}
+
+// Pass geometry and level table.  Pass 0 (D1): leaf + merging levels
+// t = 1..k1 on contiguous groups of G1 = 2^k1 slots; pass 1 (D2): levels
+// t = k1+1..h on groups of G2 = 2^(h-k1) slots at stride G1; pass 2 (U1):
+// splitting levels t = h..k1+1 on the strided groups; pass 3 (U2): levels
+// t = k1..1 and the leaf on contiguous groups.  Level.s = local slot bit,
+// Level.pad_ = t.
+void make_wide_pass(WidePass &wp, int pass, const bf_plan_s &P) {
+    const int h = P.h, k1 = P.k1, m = P.m, r = P.r, n0 = P.n0;
+    const int G1 = 1 << k1, G2 = 1 << (h - k1);
+    Stream &st = wp.st;
+    auto fill = [&](Level &lv, int kind, int K, int rpu, int nunits, int bit, int t) {
+        int upb = 1;
+        while (upb * 2 <= nunits && (long long)(upb * 2) * K * rpu <= P.wide_slot_len) upb *= 2;
+        lv.kind = kind;
+        lv.K = K;
+        lv.rpu = rpu;
+        lv.upb = upb;
+        lv.nstages = nunits / upb;
+        lv.stage_len = (upb * K * rpu + 1) & ~1;
+        lv.s = bit;
+        lv.pad_ = t;
+    };
+    int n = 0;
+    const bool contiguous = (pass == 0 || pass == 3);
+    wp.G = contiguous ? G1 : G2;
+    wp.gmul = contiguous ? G1 : 1;
+    wp.gstride = contiguous ? 1 : G1;
+    wp.ngroups = contiguous ? m / G1 : G1;
+    if (pass == 0) {
+        wp.load_kind = bfw::LD_POINTS;
+        wp.store_kind = bfw::ST_SLOTS;
+        fill(st.lev[n++], bfk::LEAF_IN, n0, r, G1, 0, 0);
+        for (int t = 1; t <= k1; ++t) fill(st.lev[n++], bfk::MERGE, 2 * r, 2 * r, G1 / 2, t - 1, t);
+    } else if (pass == 1) {
+        wp.load_kind = bfw::LD_SLOTS;
+        wp.store_kind = bfw::ST_LOGICAL;
+        for (int t = k1 + 1; t <= h; ++t) fill(st.lev[n++], bfk::MERGE, 2 * r, 2 * r, G2 / 2, t - 1 - k1, t);
+    } else if (pass == 2) {
+        wp.load_kind = bfw::LD_GATHER;
+        wp.store_kind = bfw::ST_SLOTS;
+        for (int t = h; t >= k1 + 1; --t) fill(st.lev[n++], bfk::SPLIT, 2 * r, 2 * r, G2 / 2, t - 1 - k1, t);
+    } else {
+        wp.load_kind = bfw::LD_SLOTS;
+        wp.store_kind = bfw::ST_NONE;
+        for (int t = k1; t >= 1; --t) fill(st.lev[n++], bfk::SPLIT, 2 * r, 2 * r, G1 / 2, t - 1, t);
+        fill(st.lev[n++], bfk::LEAF_OUT, r, n0, G1, 0, 0);
+    }
+    st.nlev = n;
+    st.cta_len = 0;
+    for (int i = 0; i < n; ++i) st.cta_len += (long long)st.lev[i].nstages * st.lev[i].stage_len;
+}
+
+// Packs one pass: chunk (node c, group g) = c * ngroups + g; units in the
+// order the CTA runs them; the unit matrices are the fused path's.
+void pack_wide(float2 *dst, const WidePass &wp, bool down, bool adjoint, const bf_plan_s &P, const bf_factors &f) {
+    const int L = P.L, h = P.h, m = P.m, n0 = P.n0, r = P.r;
+    const Src VL{f.VL, f.dtype, n0, r}, UL{f.UL, f.dtype, n0, r};
+    // down half reads V/H (forward) or U/G (adjoint); up half the others
+    const bool use_v = (down != adjoint);
+    const Src &LEAF = use_v ? VL : UL;
+    const Stream &st = wp.st;
+    auto work = [&](int c0, int c1) {
+        for (int c = c0; c < c1; ++c) {
+            for (int g = 0; g < wp.ngroups; ++g) {
+                float2 *o = dst + ((long long)c * wp.ngroups + g) * st.cta_len;
+                for (int li = 0; li < st.nlev; ++li) {
+                    const Level &lv = st.lev[li];
+                    const int rows = lv.upb * lv.rpu;
+                    for (int stg = 0; stg < lv.nstages; ++stg) {
+                        for (int ui = 0; ui < lv.upb; ++ui) {
+                            const int u = stg * lv.upb + ui;
+                            for (int rr = 0; rr < lv.rpu; ++rr) {
+                                for (int k = 0; k < lv.K; ++k) {
+                                    float2 v;
+                                    if (lv.kind == bfk::LEAF_IN || lv.kind == bfk::LEAF_OUT) {
+                                        const long long b = (long long)c * m + g * wp.gmul + u * wp.gstride;
+                                        v = lv.kind == bfk::LEAF_IN ? conjf2(LEAF.at(b, k, rr)) : LEAF.at(b, rr, k);
+                                    } else {
+                                        const int t = lv.pad_, sz = 1 << t, hs = sz >> 1;
+                                        const int j0 = host_insert0(u, lv.s);
+                                        const int p0 = g * wp.gmul + j0 * wp.gstride;
+                                        const int seg = p0 >> t;
+                                        const int q = host_bitrev(p0 & (hs - 1), t - 1);
+                                        const long long nodel = (long long)c * (m / sz) + seg;
+                                        const int l = L - t;
+                                        const Src X{use_v ? f.H[l - h] : f.G[l - h], f.dtype, r, 2 * r};
+                                        if (lv.kind == bfk::MERGE) {
+                                            const int cc = k / r, kp = k % r;
+                                            v = conjf2(X.at((2 * nodel + cc) * hs + q, kp, rr));
+                                        } else {
+                                            const int cc = rr / r, kk = rr % r;
+                                            v = X.at((2 * nodel + cc) * hs + q, kk, k);
+                                        }
+                                    }
+                                    o[(long long)k * rows + (long long)ui * lv.rpu + rr] = v;
+                                }
+                            }
+                        }
+                        if (lv.stage_len > rows * lv.K) o[lv.stage_len - 1] = make_float2(0.f, 0.f);
+                        o += lv.stage_len;
+                    }
+                }
+            }
+        }
+    };
+    int nthreads = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    nthreads = std::min(nthreads, m);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back(work, (int)((long long)m * t / nthreads), (int)((long long)m * (t + 1) / nthreads));
+    for (auto &th : pool) th.join();
+}
+
+bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool down, bool adjoint, const bf_factors &f) {
+    const size_t n = (size_t)P.m * wp.ngroups * wp.st.cta_len;
+    std::vector<float2> host;
+    try {
+        host.resize(n);
+    } catch (const std::bad_alloc &) {
+        return BF_ERR_NOMEM;
+    }
+    pack_wide(host.data(), wp, down, adjoint, P, f);
+    BF_CUDA(cudaMalloc(&wp.st.d, n * sizeof(float2)));
+    P.device_bytes += n * sizeof(float2);
+    BF_CUDA(cudaMemcpy(wp.st.d, host.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    return BF_OK;
+}
+
+size_t wide_smem(const bf_plan_s &P, int NR) {
+    const int G = 1 << std::max(P.k1, P.h - P.k1);
+    return bfw::wide_smem_bytes(P.wide_stages, P.wide_slot_len, G, P.W, NR);
+}
+
+// Largest RHS tile whose threads-per-unit fit the consumers and whose tile fits shared memory.
+int wide_nr_max(const bf_plan_s &P) {
+    for (int NR : {64, 32, 16}) {
+        bool ok = wide_smem(P, NR) <= (size_t)kMaxSmem;
+        for (int rpu : {P.r, 2 * P.r, P.n0}) {
+            const int rb = (rpu % 2 == 0) ? 2 : 1;
+            if ((rpu / rb) * (NR / 4) > P.consumers) ok = false;
+        }
+        if (ok) return NR;
+    }
+    return 0;
+}
+
+template <int NR>
+bf_status set_wide_attr(size_t bytes) {
+    BF_CUDA(cudaFuncSetAttribute(bfw::bf_wide_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return BF_OK;
+}
+
+template <int NR>
+cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float *d_S, const float2 *in, long long ld_in,
+                        float2 *out, long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
+    const size_t smem = wide_smem(P, NR);
+    const float2 *src[4] = {in, P.d_wsA, P.d_ws, P.d_wsA};
+    float2 *dst[4] = {P.d_wsA, P.d_ws, P.d_wsA, out};
+    const long long ldi[4] = {ld_in, P.R, P.R, P.R};
+    const long long ldo[4] = {P.R, P.R, P.R, ld_out};
+    if (tm) cudaEventRecord(tm->a, s);
+    for (int ps = 0; ps < 4; ++ps) {
+        const WidePass &wp = D.pass[ps];
+        bfw::WideParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.fac = wp.st.d;
+        p.cta_len = wp.st.cta_len;
+        p.in = src[ps];
+        p.ld_in = ldi[ps];
+        p.out = dst[ps];
+        p.ld_out = ldo[ps];
+        p.S = d_S;
+        p.err = P.d_err;
+        p.nlev = wp.st.nlev;
+        p.load_kind = wp.load_kind;
+        p.store_kind = wp.store_kind;
+        p.m = P.m;
+        p.r = P.r;
+        p.n0 = P.n0;
+        p.W = P.W;
+        p.h = P.h;
+        p.G = wp.G;
+        p.gstride = wp.gstride;
+        p.gmul = wp.gmul;
+        p.ngroups = wp.ngroups;
+        p.nrhs = nrhs;
+        p.stages = P.wide_stages;
+        p.slot_len = P.wide_slot_len;
+        for (int i = 0; i < wp.st.nlev; ++i) p.lev[i] = wp.st.lev[i];
+        const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
+        bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
+        if (tm && ps == 1) cudaEventRecord(tm->b, s);
+    }
+    if (tm) cudaEventRecord(tm->c, s);
+    return cudaGetLastError();
+}
+
 size_t plan_smem(const bf_plan_s &P, int T) { return bfk::smem_bytes(P.stages, P.slot_len, P.m, P.W, T); }
 
 template <int T>
@@ -235,6 +458,9 @@ void free_plan(bf_plan_s *P) {
         cudaFree(d->up.d);
         cudaFree(d->d_S);
     }
+    for (WideDirection *d : {&P->wfwd, &P->wadj})
+        for (auto &wp : d->pass) cudaFree(wp.st.d);
+    cudaFree(P->d_wsA);
     cudaFree(P->d_ws);
     cudaFree(P->d_stage_in);
     cudaFree(P->d_stage_out);
@@ -349,11 +575,21 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         }
         float2 *kdst = host_out ? P->d_stage_out : dst;
         if (host_out) ld_out = P->N;
-        const int T = pick_T(*P, nc);
         Timing *tm = next_timing(*P);
-        cudaError_t e = T == 4 ? launch_pair<4>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm)
-                      : T == 2 ? launch_pair<2>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm)
-                               : launch_pair<1>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm);
+        cudaError_t e;
+        if (P->wide && nc >= P->wide_min) {
+            // multi-RHS path: RHS tile = smallest of 16/32/64 covering nc, capped by the plan
+            const WideDirection &WD = adjoint ? P->wadj : P->wfwd;
+            const int NR = std::min(P->wide_nr_max, nc <= 16 ? 16 : nc <= 32 ? 32 : 64);
+            e = NR == 64 ? launch_wide<64>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm)
+              : NR == 32 ? launch_wide<32>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm)
+                         : launch_wide<16>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm);
+        } else {
+            const int T = pick_T(*P, nc);
+            e = T == 4 ? launch_pair<4>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm)
+              : T == 2 ? launch_pair<2>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm)
+                       : launch_pair<1>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm);
+        }
         if (e != cudaSuccess) return cuda_fail(e);
         if (host_out)
             BF_CUDA(cudaMemcpy2DAsync(dst, ld * 8, P->d_stage_out, P->N * 8, P->N * 8, nc, cudaMemcpyDeviceToHost, s));
@@ -475,6 +711,34 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
     if ((st = upload_stream(*P, P->adj.down, ADJ_DOWN, *f)) != BF_OK) return fail(st);
     if ((st = upload_stream(*P, P->adj.up, ADJ_UP, *f)) != BF_OK) return fail(st);
     if ((st = upload_S(*P, *f)) != BF_OK) return fail(st);
+    // Multi-RHS path for batches: built when the plan may see nrhs >= wide_min.
+    P->wide_min = env_int("BF_WIDE_MIN", 8);
+    P->wide_stages = std::max(2, env_int("BF_WIDE_STAGES", 2));
+    P->k1 = (P->h + 1) / 2;
+    {
+        int wl = env_int("BF_WIDE_SLOT_KB", 32) * 128;
+        wl = std::max(wl, std::max(4 * r * r, n0 * r + 1));
+        P->wide_slot_len = (wl + 1) & ~1;
+    }
+    P->wide_nr_max = wide_nr_max(*P);
+    if (P->nrhs_max >= P->wide_min && P->wide_nr_max > 0) {
+        P->wide = true;
+        for (int NR : {16, 32, 64}) {
+            if (NR > P->wide_nr_max) break;
+            const size_t b = wide_smem(*P, NR);
+            st = NR == 64 ? set_wide_attr<64>(b) : NR == 32 ? set_wide_attr<32>(b) : set_wide_attr<16>(b);
+            if (st != BF_OK) return fail(st);
+        }
+        for (int ps = 0; ps < 4; ++ps) {
+            make_wide_pass(P->wfwd.pass[ps], ps, *P);
+            make_wide_pass(P->wadj.pass[ps], ps, *P);
+            if ((st = upload_wide(*P, P->wfwd.pass[ps], ps < 2, false, *f)) != BF_OK) return fail(st);
+            if ((st = upload_wide(*P, P->wadj.pass[ps], ps < 2, true, *f)) != BF_OK) return fail(st);
+        }
+        const size_t wsa = (size_t)P->R * P->nrhs_max * sizeof(float2);
+        if (cudaMalloc(&P->d_wsA, wsa) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
+        P->device_bytes += wsa;
+    }
     const size_t ws = (size_t)P->R * P->nrhs_max * sizeof(float2);
     if (cudaMalloc(&P->d_ws, ws) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
     P->device_bytes += ws;

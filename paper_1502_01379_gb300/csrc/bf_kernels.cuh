@@ -135,9 +135,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 
 // --------------------------------------------------------------- producer
 // One thread streams this CTA's factor chunk, stage by stage, into the ring.
-__device__ __forceinline__ void produce(const Params &p, float2 *ring, uint64_t *full, uint64_t *empty,
+template <class P>
+__device__ __forceinline__ void produce(const P &p, long long chunk, float2 *ring, uint64_t *full, uint64_t *empty,
                                        volatile int *abort_flag) {
-    const float2 *src = p.fac + (long long)blockIdx.y * p.cta_len;
+    const float2 *src = p.fac + chunk * p.cta_len;
     uint32_t gs = 0;
     bool ok = true;
     for (int l = 0; l < p.nlev && ok; ++l) {
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(288, 1) bf_down_kernel(const Params p) {
     const int rhs0 = blockIdx.x * T;      // RHS tile (fastest: tiles of one node share its factors in L2)
     const int nt = min(T, p.nrhs - rhs0);
     if (tid >= nconsumers) {
-        if (tid == nconsumers) produce(p, s.ring, s.full, s.empty, s.abort_flag);
+        if (tid == nconsumers) produce(p, blockIdx.y, s.ring, s.full, s.empty, s.abort_flag);
     } else {
         // Input points of column node `node`: n0*m consecutive entries per RHS.
         const int nin = p.n0 * p.m;
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(288, 1) bf_up_kernel(const Params p) {
     const int rhs0 = blockIdx.x * T;      // RHS tile (fastest: tiles of one node share its factors in L2)
     const int nt = min(T, p.nrhs - rhs0);
     if (tid >= nconsumers) {
-        if (tid == nconsumers) produce(p, s.ring, s.full, s.empty, s.abort_flag);
+        if (tid == nconsumers) produce(p, blockIdx.y, s.ring, s.full, s.empty, s.abort_flag);
     } else {
         // M^h: local block q <- S[node, q] * (block q*m + node of the level-h vector).
         const int nseg = p.m * p.r;

@@ -78,6 +78,33 @@ def test_synthetic_shapes_apply_and_adjoint(bf, L, n0, r):
     plan.destroy()
 
 
+@pytest.mark.parametrize("L,n0,r", SHAPES)
+def test_multi_rhs_path_shapes(bf, L, n0, r):
+    """Batches of >= 8 vectors run the multi-pass path (groups of r-blocks in
+    bit-reversed slot order, 16/32/64 RHS per CTA): ragged tiles and several
+    passes over nrhs_max."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(L, n0, r, seed=300 + L + r, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=40)
+    for nrhs in (8, 21, 40, 83):
+        g = complex_normal((nrhs, F.N), seed=nrhs + 7, dtype=np.complex64)
+        assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+        assert _rel(_run(bf, plan, g, adjoint=True), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
+def test_multi_rhs_path_ld_and_fio(bf):
+    """Multi-RHS path on the oracle-constructed FIO (N = 4096, r = 12) with ld > N."""
+    from bfinputs import complex_normal
+    from oracle import construct
+    F = construct.construct(4096, 8, 12, "fio", seed=0).astype(np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=64)
+    g = complex_normal((64, F.N), seed=11, dtype=np.complex64)
+    assert _rel(_run(bf, plan, g, ld=F.N + 40), _oracle(F, g)) < TOL
+    assert _rel(_run(bf, plan, g, adjoint=True), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
 def test_fio_n4096_r12_against_oracle(bf):
     """1D FIO of Example 1, N = 4096, L = 8 (leaf 16), r = 12, factors built by
     the oracle's entry-sampling construction in FP64, one RHS (seed 0)."""
