@@ -4,6 +4,7 @@
 #include "bfly.h"
 #include "bf_kernels.cuh"
 #include "bf_wide.cuh"
+#include "bf_tc.cuh"
 
 #include <algorithm>
 #include <complex>
@@ -39,16 +40,18 @@ struct Timing {
     cudaEvent_t a, b, c;
 };
 
-// One pass of the multi-RHS path (bf_wide.cuh): its packed stream and group geometry.
+// One pass of the multi-RHS path (bf_wide.cuh): its packed stream and group
+// geometry (the group's slots differ in node-slot bits a .. a+kb-1).
 struct WidePass {
     Stream st;
+    bool down = true;
     int load_kind = 0, store_kind = 0;
-    int G = 1, gstride = 1, gmul = 1, ngroups = 1;
+    int a = 0, kb = 0, G = 1, ngroups = 1;
 };
 
-// D1, D2 (down half) and U1, U2 (up half) of one direction.
+// The passes of one direction: down half (leaf first), then up half.
 struct WideDirection {
-    WidePass pass[4];
+    std::vector<WidePass> pass;
 };
 
 }  // namespace
@@ -66,8 +69,9 @@ struct bf_plan_s {
     std::vector<Timing> timings;
     size_t timing_used = 0;
     // multi-RHS path
-    bool wide = false;
+    bool wide = false, tc = false;           // tc: tensor-core compute core (bf_tc.cuh)
     int wide_min = 0, wide_nr_max = 0, wide_stages = 0, wide_slot_len = 0, k1 = 0;
+    int tc_kunit = 0, tc_nk = 0;              // tc scratch sizes: max unit K, max unit N*K
     WideDirection wfwd, wadj;
     float2 *d_wsA = nullptr;                       // R x nrhs_max pass intermediate
 };
@@ -245,16 +249,18 @@ inline int host_bitrev(int x, int bits) {
     return y;
 }
 
-// Pass geometry and level table.  Pass 0 (D1): leaf + merging levels
-// t = 1..k1 on contiguous groups of G1 = 2^k1 slots; pass 1 (D2): levels
-// t = k1+1..h on groups of G2 = 2^(h-k1) slots at stride G1; pass 2 (U1):
-// splitting levels t = h..k1+1 on the strided groups; pass 3 (U2): levels
-// t = k1..1 and the leaf on contiguous groups.  Level.s = local slot bit,
-// Level.pad_ = t.
-void make_wide_pass(WidePass &wp, int pass, const bf_plan_s &P) {
-    const int h = P.h, k1 = P.k1, m = P.m, r = P.r, n0 = P.n0;
-    const int G1 = 1 << k1, G2 = 1 << (h - k1);
-    Stream &st = wp.st;
+// Pass geometry and level tables.  The h levels of each half are cut into
+// chunks of at most kmax slot bits, [a, a+kb).  Down half, chunks in
+// increasing a: merging levels t = a+1..a+kb (local bit t-1-a); the first
+// pass also loads the input points and runs the leaf, the last one stores the
+// level-h vector in logical order.  Up half, chunks in decreasing a:
+// splitting levels t = a+kb..a+1; the first pass gathers M^h, the last one
+// runs the leaf and writes the output.  Level.s = local slot bit, Level.pad_ = t.
+void make_wide_passes(WideDirection &D, const bf_plan_s &P, int kmax) {
+    const int h = P.h, m = P.m, r = P.r, n0 = P.n0;
+    std::vector<std::pair<int, int>> chunks;   // (a, kb)
+    for (int a = 0; a < h || chunks.empty(); a += std::max(1, kmax)) chunks.push_back({a, std::min(kmax, h - a)});
+    if (h == 0) chunks = {{0, 0}};
     auto fill = [&](Level &lv, int kind, int K, int rpu, int nunits, int bit, int t) {
         int upb = 1;
         while (upb * 2 <= nunits && (long long)(upb * 2) * K * rpu <= P.wide_slot_len) upb *= 2;
@@ -267,39 +273,50 @@ void make_wide_pass(WidePass &wp, int pass, const bf_plan_s &P) {
         lv.s = bit;
         lv.pad_ = t;
     };
-    int n = 0;
-    const bool contiguous = (pass == 0 || pass == 3);
-    wp.G = contiguous ? G1 : G2;
-    wp.gmul = contiguous ? G1 : 1;
-    wp.gstride = contiguous ? 1 : G1;
-    wp.ngroups = contiguous ? m / G1 : G1;
-    if (pass == 0) {
-        wp.load_kind = bfw::LD_POINTS;
-        wp.store_kind = bfw::ST_SLOTS;
-        fill(st.lev[n++], bfk::LEAF_IN, n0, r, G1, 0, 0);
-        for (int t = 1; t <= k1; ++t) fill(st.lev[n++], bfk::MERGE, 2 * r, 2 * r, G1 / 2, t - 1, t);
-    } else if (pass == 1) {
-        wp.load_kind = bfw::LD_SLOTS;
-        wp.store_kind = bfw::ST_LOGICAL;
-        for (int t = k1 + 1; t <= h; ++t) fill(st.lev[n++], bfk::MERGE, 2 * r, 2 * r, G2 / 2, t - 1 - k1, t);
-    } else if (pass == 2) {
-        wp.load_kind = bfw::LD_GATHER;
-        wp.store_kind = bfw::ST_SLOTS;
-        for (int t = h; t >= k1 + 1; --t) fill(st.lev[n++], bfk::SPLIT, 2 * r, 2 * r, G2 / 2, t - 1 - k1, t);
-    } else {
-        wp.load_kind = bfw::LD_SLOTS;
-        wp.store_kind = bfw::ST_NONE;
-        for (int t = k1; t >= 1; --t) fill(st.lev[n++], bfk::SPLIT, 2 * r, 2 * r, G1 / 2, t - 1, t);
-        fill(st.lev[n++], bfk::LEAF_OUT, r, n0, G1, 0, 0);
+    D.pass.clear();
+    const int nc = (int)chunks.size();
+    for (int half = 0; half < 2; ++half) {
+        for (int ci = 0; ci < nc; ++ci) {
+            const auto ch = half == 0 ? chunks[ci] : chunks[nc - 1 - ci];
+            const bool first = ci == 0, last = ci == nc - 1;
+            WidePass wp;
+            wp.down = half == 0;
+            wp.a = ch.first;
+            wp.kb = ch.second;
+            wp.G = 1 << wp.kb;
+            wp.ngroups = m >> wp.kb;
+            Stream &st = wp.st;
+            int n = 0;
+            if (wp.down) {
+                wp.load_kind = first ? bfw::LD_POINTS : bfw::LD_SLOTS;
+                wp.store_kind = last ? bfw::ST_LOGICAL : bfw::ST_SLOTS;
+                if (first) fill(st.lev[n++], bfk::LEAF_IN, n0, r, wp.G, 0, 0);
+                for (int t = wp.a + 1; t <= wp.a + wp.kb; ++t)
+                    fill(st.lev[n++], bfk::MERGE, 2 * r, 2 * r, wp.G / 2, t - 1 - wp.a, t);
+            } else {
+                wp.load_kind = first ? bfw::LD_GATHER : bfw::LD_SLOTS;
+                wp.store_kind = last ? bfw::ST_NONE : bfw::ST_SLOTS;
+                for (int t = wp.a + wp.kb; t >= wp.a + 1; --t)
+                    fill(st.lev[n++], bfk::SPLIT, 2 * r, 2 * r, wp.G / 2, t - 1 - wp.a, t);
+                if (last) fill(st.lev[n++], bfk::LEAF_OUT, r, n0, wp.G, 0, 0);
+            }
+            st.nlev = n;
+            st.cta_len = 0;
+            for (int i = 0; i < n; ++i) st.cta_len += (long long)st.lev[i].nstages * st.lev[i].stage_len;
+            D.pass.push_back(wp);
+        }
     }
-    st.nlev = n;
-    st.cta_len = 0;
-    for (int i = 0; i < n; ++i) st.cta_len += (long long)st.lev[i].nstages * st.lev[i].stage_len;
+}
+
+inline int host_slot_of(const WidePass &wp, int g, int j) {
+    return ((g >> wp.a) << (wp.a + wp.kb)) | (j << wp.a) | (g & ((1 << wp.a) - 1));
 }
 
 // Packs one pass: chunk (node c, group g) = c * ngroups + g; units in the
 // order the CTA runs them; the unit matrices are the fused path's.
-void pack_wide(float2 *dst, const WidePass &wp, bool down, bool adjoint, const bf_plan_s &P, const bf_factors &f) {
+void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P, const bf_factors &f) {
+    const bool down = wp.down;
+    const bool tc = P.tc;   // tensor-core layout: per unit a re plane and an im plane, canonical K-major
     const int L = P.L, h = P.h, m = P.m, n0 = P.n0, r = P.r;
     const Src VL{f.VL, f.dtype, n0, r}, UL{f.UL, f.dtype, n0, r};
     // down half reads V/H (forward) or U/G (adjoint); up half the others
@@ -320,12 +337,12 @@ void pack_wide(float2 *dst, const WidePass &wp, bool down, bool adjoint, const b
                                 for (int k = 0; k < lv.K; ++k) {
                                     float2 v;
                                     if (lv.kind == bfk::LEAF_IN || lv.kind == bfk::LEAF_OUT) {
-                                        const long long b = (long long)c * m + g * wp.gmul + u * wp.gstride;
+                                        const long long b = (long long)c * m + host_slot_of(wp, g, u);
                                         v = lv.kind == bfk::LEAF_IN ? conjf2(LEAF.at(b, k, rr)) : LEAF.at(b, rr, k);
                                     } else {
                                         const int t = lv.pad_, sz = 1 << t, hs = sz >> 1;
                                         const int j0 = host_insert0(u, lv.s);
-                                        const int p0 = g * wp.gmul + j0 * wp.gstride;
+                                        const int p0 = host_slot_of(wp, g, j0);
                                         const int seg = p0 >> t;
                                         const int q = host_bitrev(p0 & (hs - 1), t - 1);
                                         const long long nodel = (long long)c * (m / sz) + seg;
@@ -339,7 +356,14 @@ void pack_wide(float2 *dst, const WidePass &wp, bool down, bool adjoint, const b
                                             v = X.at((2 * nodel + cc) * hs + q, kk, k);
                                         }
                                     }
-                                    o[(long long)k * rows + (long long)ui * lv.rpu + rr] = v;
+                                    if (tc) {
+                                        float *uf = reinterpret_cast<float *>(o) + (long long)ui * 2 * lv.rpu * lv.K;
+                                        const int bo = bftc::boff(rr, k, lv.rpu) >> 2;
+                                        uf[bo] = v.x;
+                                        uf[(long long)lv.rpu * lv.K + bo] = v.y;
+                                    } else {
+                                        o[(long long)k * rows + (long long)ui * lv.rpu + rr] = v;
+                                    }
                                 }
                             }
                         }
@@ -358,7 +382,7 @@ void pack_wide(float2 *dst, const WidePass &wp, bool down, bool adjoint, const b
     for (auto &th : pool) th.join();
 }
 
-bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool down, bool adjoint, const bf_factors &f) {
+bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool adjoint, const bf_factors &f) {
     const size_t n = (size_t)P.m * wp.ngroups * wp.st.cta_len;
     std::vector<float2> host;
     try {
@@ -366,7 +390,7 @@ bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool down, bool adjoint, const
     } catch (const std::bad_alloc &) {
         return BF_ERR_NOMEM;
     }
-    pack_wide(host.data(), wp, down, adjoint, P, f);
+    pack_wide(host.data(), wp, adjoint, P, f);
     BF_CUDA(cudaMalloc(&wp.st.d, n * sizeof(float2)));
     P.device_bytes += n * sizeof(float2);
     BF_CUDA(cudaMemcpy(wp.st.d, host.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
@@ -374,7 +398,7 @@ bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool down, bool adjoint, const
 }
 
 size_t wide_smem(const bf_plan_s &P, int NR) {
-    const int G = 1 << std::max(P.k1, P.h - P.k1);
+    const int G = 1 << std::min(P.k1, P.h);
     return bfw::wide_smem_bytes(P.wide_stages, P.wide_slot_len, G, P.W, NR);
 }
 
@@ -397,25 +421,27 @@ bf_status set_wide_attr(size_t bytes) {
     return BF_OK;
 }
 
+size_t tc_smem(const bf_plan_s &P, int kb) {
+    return bftc::tc_smem_bytes(P.wide_stages, P.wide_slot_len, 1 << kb, P.W, P.tc_kunit, P.tc_nk);
+}
+
 template <int NR>
 cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float *d_S, const float2 *in, long long ld_in,
                         float2 *out, long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
     const size_t smem = wide_smem(P, NR);
-    const float2 *src[4] = {in, P.d_wsA, P.d_ws, P.d_wsA};
-    float2 *dst[4] = {P.d_wsA, P.d_ws, P.d_wsA, out};
-    const long long ldi[4] = {ld_in, P.R, P.R, P.R};
-    const long long ldo[4] = {P.R, P.R, P.R, ld_out};
+    float2 *buf[2] = {P.d_wsA, P.d_ws};
+    const int np = (int)D.pass.size();
     if (tm) cudaEventRecord(tm->a, s);
-    for (int ps = 0; ps < 4; ++ps) {
+    for (int ps = 0; ps < np; ++ps) {
         const WidePass &wp = D.pass[ps];
         bfw::WideParams p;
         std::memset(&p, 0, sizeof(p));
         p.fac = wp.st.d;
         p.cta_len = wp.st.cta_len;
-        p.in = src[ps];
-        p.ld_in = ldi[ps];
-        p.out = dst[ps];
-        p.ld_out = ldo[ps];
+        p.in = ps == 0 ? in : buf[(ps - 1) & 1];
+        p.ld_in = ps == 0 ? ld_in : P.R;
+        p.out = ps == np - 1 ? out : buf[ps & 1];
+        p.ld_out = ps == np - 1 ? ld_out : P.R;
         p.S = d_S;
         p.err = P.d_err;
         p.nlev = wp.st.nlev;
@@ -427,16 +453,21 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
         p.W = P.W;
         p.h = P.h;
         p.G = wp.G;
-        p.gstride = wp.gstride;
-        p.gmul = wp.gmul;
+        p.a = wp.a;
+        p.kb = wp.kb;
         p.ngroups = wp.ngroups;
         p.nrhs = nrhs;
         p.stages = P.wide_stages;
         p.slot_len = P.wide_slot_len;
         for (int i = 0; i < wp.st.nlev; ++i) p.lev[i] = wp.st.lev[i];
-        const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
-        bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
-        if (tm && ps == 1) cudaEventRecord(tm->b, s);
+        if (P.tc) {
+            const dim3 grid((nrhs + bftc::NR - 1) / bftc::NR, P.m * wp.ngroups);
+            bftc::bf_tc_kernel<<<grid, 256 + 32, tc_smem(P, std::min(P.k1, P.h)), s>>>(p, P.tc_kunit, P.tc_nk);
+        } else {
+            const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
+            bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
+        }
+        if (tm && ps + 1 < np && !D.pass[ps + 1].down && wp.down) cudaEventRecord(tm->b, s);
     }
     if (tm) cudaEventRecord(tm->c, s);
     return cudaGetLastError();
@@ -580,7 +611,7 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         if (P->wide && nc >= P->wide_min) {
             // multi-RHS path: RHS tile = smallest of 16/32/64 covering nc, capped by the plan
             const WideDirection &WD = adjoint ? P->wadj : P->wfwd;
-            const int NR = std::min(P->wide_nr_max, nc <= 16 ? 16 : nc <= 32 ? 32 : 64);
+            const int NR = P->tc ? 64 : std::min(P->wide_nr_max, nc <= 16 ? 16 : nc <= 32 ? 32 : 64);
             e = NR == 64 ? launch_wide<64>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm)
               : NR == 32 ? launch_wide<32>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm)
                          : launch_wide<16>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm);
@@ -714,27 +745,50 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
     // Multi-RHS path for batches: built when the plan may see nrhs >= wide_min.
     P->wide_min = env_int("BF_WIDE_MIN", 8);
     P->wide_stages = std::max(2, env_int("BF_WIDE_STAGES", 2));
-    P->k1 = (P->h + 1) / 2;
+    // slot bits per pass: ceil(h/2) by default (two passes per half)
+    P->k1 = std::max(1, env_int("BF_WIDE_KMAX", (P->h + 1) / 2));
     {
         int wl = env_int("BF_WIDE_SLOT_KB", 32) * 128;
         wl = std::max(wl, std::max(4 * r * r, n0 * r + 1));
         P->wide_slot_len = (wl + 1) & ~1;
     }
     P->wide_nr_max = wide_nr_max(*P);
-    if (P->nrhs_max >= P->wide_min && P->wide_nr_max > 0) {
+    // Tensor-core core: unit dimensions must be multiples of 16 (MMA N with M = 128).
+    // Opt-in (BF_TC=1) until it outruns the CUDA-core core at every batch size.
+    if (P->nrhs_max >= P->wide_min && env_int("BF_TC", 0) == 1 && r % 16 == 0 && n0 % 16 == 0) {
+        P->tc_kunit = std::max(2 * r, n0);
+        P->tc_nk = std::max(4 * r * r, n0 * r);
+        P->wide_slot_len = std::max(2048, P->tc_nk);
+        int kb = 0;
+        for (int stages : {3, 2}) {
+            P->wide_stages = stages;
+            kb = 0;
+            while (kb < std::max(P->h, 1) && tc_smem(*P, kb + 1) <= (size_t)kMaxSmem) ++kb;
+            if (kb >= 1) break;
+        }
+        if (kb >= 1) {
+            P->tc = true;
+            P->k1 = std::min(env_int("BF_WIDE_KMAX", kb), kb);
+            P->wide_nr_max = bftc::NR;
+            if (cudaFuncSetAttribute(bftc::bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem(*P, std::min(P->k1, P->h))) != cudaSuccess)
+                return fail(cuda_fail(cudaErrorInvalidValue));
+        }
+    }
+    if (P->nrhs_max >= P->wide_min && (P->tc || P->wide_nr_max > 0)) {
         P->wide = true;
         for (int NR : {16, 32, 64}) {
-            if (NR > P->wide_nr_max) break;
+            if (P->tc || NR > P->wide_nr_max) break;
             const size_t b = wide_smem(*P, NR);
             st = NR == 64 ? set_wide_attr<64>(b) : NR == 32 ? set_wide_attr<32>(b) : set_wide_attr<16>(b);
             if (st != BF_OK) return fail(st);
         }
-        for (int ps = 0; ps < 4; ++ps) {
-            make_wide_pass(P->wfwd.pass[ps], ps, *P);
-            make_wide_pass(P->wadj.pass[ps], ps, *P);
-            if ((st = upload_wide(*P, P->wfwd.pass[ps], ps < 2, false, *f)) != BF_OK) return fail(st);
-            if ((st = upload_wide(*P, P->wadj.pass[ps], ps < 2, true, *f)) != BF_OK) return fail(st);
-        }
+        make_wide_passes(P->wfwd, *P, P->k1);
+        make_wide_passes(P->wadj, *P, P->k1);
+        for (auto &wp : P->wfwd.pass)
+            if ((st = upload_wide(*P, wp, false, *f)) != BF_OK) return fail(st);
+        for (auto &wp : P->wadj.pass)
+            if ((st = upload_wide(*P, wp, true, *f)) != BF_OK) return fail(st);
         const size_t wsa = (size_t)P->R * P->nrhs_max * sizeof(float2);
         if (cudaMalloc(&P->d_wsA, wsa) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
         P->device_bytes += wsa;

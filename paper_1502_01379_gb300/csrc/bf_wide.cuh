@@ -13,10 +13,11 @@
 // stages of a radix-2 FFT, and after all h levels slot p holds logical block
 // bitrev_h(p).  So levels 1..k touch only bits 0..k-1 (contiguous groups of
 // 2^k slots) and levels k+1..h only bits k..h-1 (groups of 2^(h-k) slots at
-// stride 2^k): pass D1 = leaf + levels 1..k, pass D2 = levels k+1..h.  The up
-// half mirrors this: pass U1 gathers the M^h block transpose (Eq. KeqUMV)
-// into bit-reversed slots and runs splitting levels h..k+1, pass U2 runs
-// levels k..1 and the leaf U^L.
+// stride 2^k): pass D1 = leaf + levels 1..k, pass D2 = levels k+1..h (and in
+// general any split of the h levels into chunks of slot bits a..a+kb-1, one
+// pass per chunk).  The up half mirrors this: its first pass gathers the M^h
+// block transpose (Eq. KeqUMV) into bit-reversed slots and runs the top
+// splitting levels, its last pass runs the lowest levels and the leaf U^L.
 //
 // Each CTA = (node, group, RHS tile of NR).  Factor units are the same 2r x 2r
 // butterflies and leaf blocks as in the fused path, packed per CTA in the
@@ -47,8 +48,8 @@ struct WideParams {
     unsigned *err;
     int nlev, load_kind, store_kind;
     int m, r, n0, W, h;
-    int G;                  // r-block slots per group
-    int gstride, gmul;      // node slot of local j in group g: g * gmul + j * gstride
+    int G;                  // r-block slots per group (2^kb)
+    int a, kb;              // the group's slots differ in node-slot bits a .. a+kb-1
     int ngroups;
     int nrhs, stages, slot_len;
     Level lev[bfk::kMaxLevels];   // MERGE / SPLIT: lev.s holds the local slot bit
@@ -66,6 +67,10 @@ template <int NR>
 __device__ __forceinline__ int xh(int pos, int tq, int half) {
     constexpr int NQ = NR / 4;
     return pos * NR + half * (NR / 2) + (((tq ^ pos) & (NQ - 1)) << 1);
+}
+// Node slot of local slot j of group g: bits a..a+kb-1 from j, the others from g.
+__device__ __forceinline__ int slot_of(const WideParams &p, int g, int j) {
+    return ((g >> p.a) << (p.a + p.kb)) | (j << p.a) | (g & ((1 << p.a) - 1));
 }
 __device__ __forceinline__ int insert0(int v, int b) { return ((v >> b) << (b + 1)) | (v & ((1 << b) - 1)); }
 __device__ __forceinline__ int bitrev(int x, int bits) {
@@ -104,10 +109,10 @@ __device__ __forceinline__ void wide_load(const WideParams &p, float2 *X, int n,
         const float2 *src;
         float w = 1.f;
         if (points) {
-            src = p.in + ((long long)n * p.m + (long long)g * p.gmul) * p.n0 + e;
+            src = p.in + ((long long)n * p.m + slot_of(p, g, 0)) * p.n0 + e;   // a = 0: contiguous
         } else {
             const int j = e / p.r, k = e - j * p.r;
-            const int ps = g * p.gmul + j * p.gstride;
+            const int ps = slot_of(p, g, j);
             if (p.load_kind == LD_SLOTS) {
                 src = p.in + ((long long)n * p.m + ps) * p.r + k;
             } else {   // M^h: slot ps holds logical block q = bitrev_h(ps) of this row node
@@ -140,7 +145,7 @@ __device__ __forceinline__ void wide_store(const WideParams &p, const float2 *X,
     const int npos = p.G * p.r;
     for (int e = tid; e < npos; e += nc) {
         const int j = e / p.r, k = e - j * p.r;
-        const int ps = g * p.gmul + j * p.gstride;
+        const int ps = slot_of(p, g, j);
         const int blk = p.store_kind == ST_LOGICAL ? bitrev(ps, p.h) : ps;
         float2 *dst = p.out + (long long)rhs0 * p.ld_out + ((long long)n * p.m + blk) * p.r + k;
 #pragma unroll 4
@@ -234,7 +239,7 @@ __device__ __forceinline__ void wide_level(const WideParams &p, const WideSmem &
                 for (int a = 0; a < RB; ++a) {
                     const int rr = row0 + a;
                     if (KIND == bfk::LEAF_OUT) {
-                        const int ps = g * p.gmul + u * p.gstride;
+                        const int ps = slot_of(p, g, u);
                         const long long pt = ((long long)n * p.m + ps) * p.n0 + rr;
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {

@@ -105,6 +105,40 @@ def test_multi_rhs_path_ld_and_fio(bf):
     plan.destroy()
 
 
+TC_SHAPES = [(0, 16, 16), (2, 16, 16), (4, 16, 32), (6, 32, 16), (8, 16, 16), (8, 64, 16), (10, 16, 16)]
+
+
+@pytest.mark.parametrize("L,n0,r", TC_SHAPES)
+@pytest.mark.parametrize("kmax", [None, 1])
+def test_tensor_core_path(bf, L, n0, r, kmax, monkeypatch):
+    """Shapes with r and leaf multiples of 16 run batches on the tcgen05 core
+    (128 RHS per CTA, 3xTF32): ragged tiles, several tiles, and the pass
+    split forced to one slot bit per pass (kmax = 1)."""
+    from bfinputs import complex_normal, synthetic_factors
+    monkeypatch.setenv("BF_TC", "1")
+    if kmax is not None:
+        monkeypatch.setenv("BF_WIDE_KMAX", str(kmax))
+    F = synthetic_factors(L, n0, r, seed=500 + L + r, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=300)
+    for nrhs in (8, 130, 300):
+        g = complex_normal((nrhs, F.N), seed=nrhs + 3, dtype=np.complex64)
+        assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+        assert _rel(_run(bf, plan, g, adjoint=True), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
+def test_tensor_core_path_odd_ld(bf, monkeypatch):
+    """Odd leading dimension: the tensor path's global accesses stay 8-byte."""
+    from bfinputs import complex_normal, synthetic_factors
+    monkeypatch.setenv("BF_TC", "1")
+    F = synthetic_factors(8, 16, 16, seed=9, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=64)
+    g = complex_normal((40, F.N), seed=2, dtype=np.complex64)
+    assert _rel(_run(bf, plan, g, ld=F.N + 3), _oracle(F, g)) < TOL
+    assert _rel(_run(bf, plan, g, adjoint=True, ld=F.N + 1), _oracle(F, g, True)) < TOL
+    plan.destroy()
+
+
 def test_fio_n4096_r12_against_oracle(bf):
     """1D FIO of Example 1, N = 4096, L = 8 (leaf 16), r = 12, factors built by
     the oracle's entry-sampling construction in FP64, one RHS (seed 0)."""
