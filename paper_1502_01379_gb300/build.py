@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libbfly.so")
 SOURCES = [os.path.join(CSRC, "bf_capi.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "bf_kernels.cuh"), os.path.join(INCLUDE, "bfly.h")]
+DEPS = SOURCES + [os.path.join(CSRC, n) for n in sorted(os.listdir(CSRC)) if n.endswith(".cuh")] + [
+    os.path.join(INCLUDE, "bfly.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -49,8 +49,19 @@ struct WidePass {
     int a = 0, kb = 0, G = 1, ngroups = 1;
 };
 
+// Configuration of one multi-RHS core: CUDA-core (bf_wide.cuh) or tensor-core (bf_tc.cuh).
+struct WideCfg {
+    bool tc = false;
+    int kmax = 1;          // slot bits per pass
+    int slot_len = 0;      // ring slot, complex entries
+    int stages = 2;
+    int nr_max = 0;        // CUDA-core: largest RHS tile
+    int dn = 0, nk = 0;    // tensor-core: accumulator columns per buffer, max unit N*K
+};
+
 // The passes of one direction: down half (leaf first), then up half.
 struct WideDirection {
+    WideCfg cfg;
     std::vector<WidePass> pass;
 };
 
@@ -69,10 +80,11 @@ struct bf_plan_s {
     std::vector<Timing> timings;
     size_t timing_used = 0;
     // multi-RHS path
-    bool wide = false, tc = false;           // tc: tensor-core compute core (bf_tc.cuh)
-    int wide_min = 0, wide_nr_max = 0, wide_stages = 0, wide_slot_len = 0, k1 = 0;
-    int tc_kunit = 0, tc_nk = 0;              // tc scratch sizes: max unit K, max unit N*K
-    WideDirection wfwd, wadj;
+    bool wide = false, tc = false;           // which multi-RHS cores were built
+    int wide_min = 0, tc_min = 0;             // smallest batch each core serves
+    int num_sms = 1;
+    WideDirection wfwd, wadj;                 // CUDA-core multi-RHS passes
+    WideDirection tfwd, tadj;                 // tensor-core multi-RHS passes
     float2 *d_wsA = nullptr;                       // R x nrhs_max pass intermediate
 };
 
@@ -256,14 +268,16 @@ inline int host_bitrev(int x, int bits) {
 // level-h vector in logical order.  Up half, chunks in decreasing a:
 // splitting levels t = a+kb..a+1; the first pass gathers M^h, the last one
 // runs the leaf and writes the output.  Level.s = local slot bit, Level.pad_ = t.
-void make_wide_passes(WideDirection &D, const bf_plan_s &P, int kmax) {
+void make_wide_passes(WideDirection &D, const bf_plan_s &P, const WideCfg &cfg) {
     const int h = P.h, m = P.m, r = P.r, n0 = P.n0;
+    const int kmax = cfg.kmax;
+    D.cfg = cfg;
     std::vector<std::pair<int, int>> chunks;   // (a, kb)
     for (int a = 0; a < h || chunks.empty(); a += std::max(1, kmax)) chunks.push_back({a, std::min(kmax, h - a)});
     if (h == 0) chunks = {{0, 0}};
     auto fill = [&](Level &lv, int kind, int K, int rpu, int nunits, int bit, int t) {
         int upb = 1;
-        while (upb * 2 <= nunits && (long long)(upb * 2) * K * rpu <= P.wide_slot_len) upb *= 2;
+        while (upb * 2 <= nunits && (long long)(upb * 2) * K * rpu <= cfg.slot_len) upb *= 2;
         lv.kind = kind;
         lv.K = K;
         lv.rpu = rpu;
@@ -314,9 +328,8 @@ inline int host_slot_of(const WidePass &wp, int g, int j) {
 
 // Packs one pass: chunk (node c, group g) = c * ngroups + g; units in the
 // order the CTA runs them; the unit matrices are the fused path's.
-void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P, const bf_factors &f) {
-    const bool down = wp.down;
-    const bool tc = P.tc;   // tensor-core layout: per unit a re plane and an im plane, canonical K-major
+void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P, const bf_factors &f, bool tc) {
+    const bool down = wp.down;   // tc: tensor-core layout, per unit one K-major operand [Re B; Im B]
     const int L = P.L, h = P.h, m = P.m, n0 = P.n0, r = P.r;
     const Src VL{f.VL, f.dtype, n0, r}, UL{f.UL, f.dtype, n0, r};
     // down half reads V/H (forward) or U/G (adjoint); up half the others
@@ -356,11 +369,10 @@ void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P
                                             v = X.at((2 * nodel + cc) * hs + q, kk, k);
                                         }
                                     }
-                                    if (tc) {
+                                    if (tc) {   // one operand of 2N rows: [Re B; Im B]
                                         float *uf = reinterpret_cast<float *>(o) + (long long)ui * 2 * lv.rpu * lv.K;
-                                        const int bo = bftc::boff(rr, k, lv.rpu) >> 2;
-                                        uf[bo] = v.x;
-                                        uf[(long long)lv.rpu * lv.K + bo] = v.y;
+                                        uf[bftc::boff(rr, k, 2 * lv.rpu) >> 2] = v.x;
+                                        uf[bftc::boff(lv.rpu + rr, k, 2 * lv.rpu) >> 2] = v.y;
                                     } else {
                                         o[(long long)k * rows + (long long)ui * lv.rpu + rr] = v;
                                     }
@@ -382,7 +394,7 @@ void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P
     for (auto &th : pool) th.join();
 }
 
-bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool adjoint, const bf_factors &f) {
+bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool adjoint, const bf_factors &f, bool tc) {
     const size_t n = (size_t)P.m * wp.ngroups * wp.st.cta_len;
     std::vector<float2> host;
     try {
@@ -390,22 +402,22 @@ bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool adjoint, const bf_factors
     } catch (const std::bad_alloc &) {
         return BF_ERR_NOMEM;
     }
-    pack_wide(host.data(), wp, adjoint, P, f);
+    pack_wide(host.data(), wp, adjoint, P, f, tc);
     BF_CUDA(cudaMalloc(&wp.st.d, n * sizeof(float2)));
     P.device_bytes += n * sizeof(float2);
     BF_CUDA(cudaMemcpy(wp.st.d, host.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
     return BF_OK;
 }
 
-size_t wide_smem(const bf_plan_s &P, int NR) {
-    const int G = 1 << std::min(P.k1, P.h);
-    return bfw::wide_smem_bytes(P.wide_stages, P.wide_slot_len, G, P.W, NR);
+size_t wide_smem(const bf_plan_s &P, const WideCfg &c, int NR) {
+    const int G = 1 << std::min(c.kmax, P.h);
+    return bfw::wide_smem_bytes(c.stages, c.slot_len, G, P.W, NR);
 }
 
 // Largest RHS tile whose threads-per-unit fit the consumers and whose tile fits shared memory.
-int wide_nr_max(const bf_plan_s &P) {
+int wide_nr_max(const bf_plan_s &P, const WideCfg &c) {
     for (int NR : {64, 32, 16}) {
-        bool ok = wide_smem(P, NR) <= (size_t)kMaxSmem;
+        bool ok = wide_smem(P, c, NR) <= (size_t)kMaxSmem;
         for (int rpu : {P.r, 2 * P.r, P.n0}) {
             const int rb = (rpu % 2 == 0) ? 2 : 1;
             if ((rpu / rb) * (NR / 4) > P.consumers) ok = false;
@@ -421,14 +433,18 @@ bf_status set_wide_attr(size_t bytes) {
     return BF_OK;
 }
 
-size_t tc_smem(const bf_plan_s &P, int kb) {
-    return bftc::tc_smem_bytes(P.wide_stages, P.wide_slot_len, 1 << kb, P.W, P.tc_kunit, P.tc_nk);
+// RHS capacity of the workspaces: the tensor-core core pads to whole 128-RHS tiles.
+long long ws_rhs(const bf_plan_s &P) {
+    return P.tc ? (long long)(P.nrhs_max + bftc::NR - 1) / bftc::NR * bftc::NR : P.nrhs_max;
 }
+
+size_t tc_smem(const WideCfg &c) { return bftc::tc_smem_bytes(c.stages, c.slot_len, c.nk); }
 
 template <int NR>
 cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float *d_S, const float2 *in, long long ld_in,
                         float2 *out, long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
-    const size_t smem = wide_smem(P, NR);
+    const WideCfg &c = D.cfg;
+    const size_t smem = c.tc ? tc_smem(c) : wide_smem(P, c, NR);
     float2 *buf[2] = {P.d_wsA, P.d_ws};
     const int np = (int)D.pass.size();
     if (tm) cudaEventRecord(tm->a, s);
@@ -438,10 +454,14 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
         std::memset(&p, 0, sizeof(p));
         p.fac = wp.st.d;
         p.cta_len = wp.st.cta_len;
+        // tensor-core core: intermediates [position][RHS] (RHS padded to the 128-row tile)
+        const long long ldt = c.tc ? (long long)(nrhs + bftc::NR - 1) / bftc::NR * bftc::NR : P.R;
         p.in = ps == 0 ? in : buf[(ps - 1) & 1];
-        p.ld_in = ps == 0 ? ld_in : P.R;
+        p.ld_in = ps == 0 ? ld_in : ldt;
         p.out = ps == np - 1 ? out : buf[ps & 1];
-        p.ld_out = ps == np - 1 ? ld_out : P.R;
+        p.ld_out = ps == np - 1 ? ld_out : ldt;
+        p.in_t = c.tc && ps > 0;
+        p.out_t = c.tc && ps < np - 1;
         p.S = d_S;
         p.err = P.d_err;
         p.nlev = wp.st.nlev;
@@ -457,12 +477,13 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
         p.kb = wp.kb;
         p.ngroups = wp.ngroups;
         p.nrhs = nrhs;
-        p.stages = P.wide_stages;
-        p.slot_len = P.wide_slot_len;
+        p.stages = c.stages;
+        p.slot_len = c.slot_len;
         for (int i = 0; i < wp.st.nlev; ++i) p.lev[i] = wp.st.lev[i];
-        if (P.tc) {
-            const dim3 grid((nrhs + bftc::NR - 1) / bftc::NR, P.m * wp.ngroups);
-            bftc::bf_tc_kernel<<<grid, 256 + 32, tc_smem(P, std::min(P.k1, P.h)), s>>>(p, P.tc_kunit, P.tc_nk);
+        if (c.tc) {
+            const long long items = (long long)((nrhs + bftc::NR - 1) / bftc::NR) * P.m * wp.ngroups;
+            const int grid = (int)std::min<long long>(items, P.num_sms);   // persistent: one CTA per SM
+            bftc::bf_tc_kernel<<<grid, bftc::kTcThreads, tc_smem(c), s>>>(p, c.nk, c.dn);
         } else {
             const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
             bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
@@ -489,7 +510,7 @@ void free_plan(bf_plan_s *P) {
         cudaFree(d->up.d);
         cudaFree(d->d_S);
     }
-    for (WideDirection *d : {&P->wfwd, &P->wadj})
+    for (WideDirection *d : {&P->wfwd, &P->wadj, &P->tfwd, &P->tadj})
         for (auto &wp : d->pass) cudaFree(wp.st.d);
     cudaFree(P->d_wsA);
     cudaFree(P->d_ws);
@@ -608,10 +629,13 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         if (host_out) ld_out = P->N;
         Timing *tm = next_timing(*P);
         cudaError_t e;
-        if (P->wide && nc >= P->wide_min) {
-            // multi-RHS path: RHS tile = smallest of 16/32/64 covering nc, capped by the plan
+        if (P->tc && nc >= P->tc_min) {
+            // tensor-core multi-RHS core (128 RHS per CTA)
+            e = launch_wide<64>(*P, adjoint ? P->tadj : P->tfwd, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm);
+        } else if (P->wide && nc >= P->wide_min) {
+            // CUDA-core multi-RHS core: RHS tile = smallest of 16/32/64 covering nc, capped by the plan
             const WideDirection &WD = adjoint ? P->wadj : P->wfwd;
-            const int NR = P->tc ? 64 : std::min(P->wide_nr_max, nc <= 16 ? 16 : nc <= 32 ? 32 : 64);
+            const int NR = std::min(WD.cfg.nr_max, nc <= 16 ? 16 : nc <= 32 ? 32 : 64);
             e = NR == 64 ? launch_wide<64>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm)
               : NR == 32 ? launch_wide<32>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm)
                          : launch_wide<16>(*P, WD, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm);
@@ -742,58 +766,72 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
     if ((st = upload_stream(*P, P->adj.down, ADJ_DOWN, *f)) != BF_OK) return fail(st);
     if ((st = upload_stream(*P, P->adj.up, ADJ_UP, *f)) != BF_OK) return fail(st);
     if ((st = upload_S(*P, *f)) != BF_OK) return fail(st);
-    // Multi-RHS path for batches: built when the plan may see nrhs >= wide_min.
-    P->wide_min = env_int("BF_WIDE_MIN", 8);
-    P->wide_stages = std::max(2, env_int("BF_WIDE_STAGES", 2));
-    // slot bits per pass: ceil(h/2) by default (two passes per half)
-    P->k1 = std::max(1, env_int("BF_WIDE_KMAX", (P->h + 1) / 2));
     {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            P->num_sms = 1;
+        cudaGetLastError();
+    }
+    // Multi-RHS cores for batches.  CUDA-core: built when the plan may see
+    // nrhs >= wide_min (8).  Tensor-core: built when nrhs_max >= tc_min (128)
+    // and the unit dimensions are multiples of 16 (MMA N with M = 128 RHS);
+    // each call uses the tensor-core core for batches of at least tc_min.
+    P->wide_min = env_int("BF_WIDE_MIN", 8);
+    P->tc_min = env_int("BF_TC_MIN", 128);
+    if (P->nrhs_max >= P->wide_min) {
+        WideCfg c;
+        c.tc = false;
+        c.stages = std::max(2, env_int("BF_WIDE_STAGES", 2));
+        c.kmax = std::max(1, env_int("BF_WIDE_KMAX", (P->h + 1) / 2));   // two passes per half
         int wl = env_int("BF_WIDE_SLOT_KB", 32) * 128;
         wl = std::max(wl, std::max(4 * r * r, n0 * r + 1));
-        P->wide_slot_len = (wl + 1) & ~1;
+        c.slot_len = (wl + 1) & ~1;
+        c.nr_max = wide_nr_max(*P, c);
+        if (c.nr_max > 0) {
+            P->wide = true;
+            for (int NR : {16, 32, 64}) {
+                if (NR > c.nr_max) break;
+                const size_t b = wide_smem(*P, c, NR);
+                st = NR == 64 ? set_wide_attr<64>(b) : NR == 32 ? set_wide_attr<32>(b) : set_wide_attr<16>(b);
+                if (st != BF_OK) return fail(st);
+            }
+            make_wide_passes(P->wfwd, *P, c);
+            make_wide_passes(P->wadj, *P, c);
+        }
     }
-    P->wide_nr_max = wide_nr_max(*P);
-    // Tensor-core core: unit dimensions must be multiples of 16 (MMA N with M = 128).
-    // Opt-in (BF_TC=1) until it outruns the CUDA-core core at every batch size.
-    if (P->nrhs_max >= P->wide_min && env_int("BF_TC", 0) == 1 && r % 16 == 0 && n0 % 16 == 0) {
-        P->tc_kunit = std::max(2 * r, n0);
-        P->tc_nk = std::max(4 * r * r, n0 * r);
-        P->wide_slot_len = std::max(2048, P->tc_nk);
+    if (P->nrhs_max >= std::max(P->tc_min, 1) && env_int("BF_TC", 1) == 1 && r % 16 == 0 && n0 % 16 == 0) {
+        WideCfg c;
+        c.tc = true;
+        c.dn = 2 * std::max(2 * r, n0);
+        c.nk = std::max(4 * r * r, n0 * r);
+        c.slot_len = std::max(2048, c.nk);
+        c.stages = 3;
+        // group size: as many slot bits as the tensor-memory tile allows
         int kb = 0;
-        for (int stages : {3, 2}) {
-            P->wide_stages = stages;
-            kb = 0;
-            while (kb < std::max(P->h, 1) && tc_smem(*P, kb + 1) <= (size_t)kMaxSmem) ++kb;
-            if (kb >= 1) break;
-        }
-        if (kb >= 1) {
+        while (kb < std::max(P->h, 1) && bftc::tc_tmem_fits((1 << (kb + 1)) * P->W, c.dn)) ++kb;
+        c.kmax = std::min(env_int("BF_TC_KMAX", kb), kb);
+        c.nr_max = bftc::NR;
+        if (kb >= 1 && tc_smem(c) <= (size_t)kMaxSmem) {
             P->tc = true;
-            P->k1 = std::min(env_int("BF_WIDE_KMAX", kb), kb);
-            P->wide_nr_max = bftc::NR;
             if (cudaFuncSetAttribute(bftc::bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tc_smem(*P, std::min(P->k1, P->h))) != cudaSuccess)
+                                     (int)tc_smem(c)) != cudaSuccess)
                 return fail(cuda_fail(cudaErrorInvalidValue));
+            make_wide_passes(P->tfwd, *P, c);
+            make_wide_passes(P->tadj, *P, c);
         }
     }
-    if (P->nrhs_max >= P->wide_min && (P->tc || P->wide_nr_max > 0)) {
-        P->wide = true;
-        for (int NR : {16, 32, 64}) {
-            if (P->tc || NR > P->wide_nr_max) break;
-            const size_t b = wide_smem(*P, NR);
-            st = NR == 64 ? set_wide_attr<64>(b) : NR == 32 ? set_wide_attr<32>(b) : set_wide_attr<16>(b);
-            if (st != BF_OK) return fail(st);
-        }
-        make_wide_passes(P->wfwd, *P, P->k1);
-        make_wide_passes(P->wadj, *P, P->k1);
-        for (auto &wp : P->wfwd.pass)
-            if ((st = upload_wide(*P, wp, false, *f)) != BF_OK) return fail(st);
-        for (auto &wp : P->wadj.pass)
-            if ((st = upload_wide(*P, wp, true, *f)) != BF_OK) return fail(st);
-        const size_t wsa = (size_t)P->R * P->nrhs_max * sizeof(float2);
+    for (auto *D : {&P->wfwd, &P->wadj, &P->tfwd, &P->tadj}) {
+        const bool adj = (D == &P->wadj || D == &P->tadj);
+        for (auto &wp : D->pass)
+            if ((st = upload_wide(*P, wp, adj, *f, D->cfg.tc)) != BF_OK) return fail(st);
+    }
+    if (P->wide || P->tc) {
+        const size_t wsa = (size_t)P->R * ws_rhs(*P) * sizeof(float2);
         if (cudaMalloc(&P->d_wsA, wsa) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
         P->device_bytes += wsa;
     }
-    const size_t ws = (size_t)P->R * P->nrhs_max * sizeof(float2);
+    const size_t ws = (size_t)P->R * ws_rhs(*P) * sizeof(float2);
     if (cudaMalloc(&P->d_ws, ws) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
     P->device_bytes += ws;
     if (cudaMalloc(&P->d_err, sizeof(unsigned)) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));

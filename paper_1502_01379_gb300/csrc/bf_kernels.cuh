@@ -135,21 +135,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 
 // --------------------------------------------------------------- producer
 // One thread streams this CTA's factor chunk, stage by stage, into the ring.
+// Streams one factor chunk (all levels of one CTA work item) into the ring;
+// `gs` counts stages across calls.  Returns false if a wait gave up.
 template <class P>
-__device__ __forceinline__ void produce(const P &p, long long chunk, float2 *ring, uint64_t *full, uint64_t *empty,
-                                       volatile int *abort_flag) {
+__device__ __forceinline__ bool produce_chunk(const P &p, long long chunk, uint32_t &gs, float2 *ring, uint64_t *full,
+                                              uint64_t *empty, volatile int *abort_flag) {
     const float2 *src = p.fac + chunk * p.cta_len;
-    uint32_t gs = 0;
-    bool ok = true;
-    for (int l = 0; l < p.nlev && ok; ++l) {
+    for (int l = 0; l < p.nlev; ++l) {
         const Level &lv = p.lev[l];
         for (int st = 0; st < lv.nstages; ++st) {
             const uint32_t slot = gs % p.stages;
             const uint32_t use = gs / p.stages;
-            if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, abort_flag, p.err)) {
-                ok = false;
-                break;
-            }
+            if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, abort_flag, p.err)) return false;
             const uint32_t bytes = (uint32_t)lv.stage_len * 8u;
             mbar_arrive_expect_tx(&full[slot], bytes);
             bulk_g2s(ring + (long long)slot * p.slot_len, src, bytes, &full[slot]);
@@ -157,7 +154,12 @@ __device__ __forceinline__ void produce(const P &p, long long chunk, float2 *rin
             ++gs;
         }
     }
-    // Drain: every copy issued must have landed before the CTA may exit.
+    return true;
+}
+
+// Every copy issued must have landed before the CTA may exit.
+template <class P>
+__device__ __forceinline__ void produce_drain(const P &p, uint32_t gs, uint64_t *full, volatile int *abort_flag) {
     for (uint32_t slot = 0; slot < (uint32_t)p.stages && slot < gs; ++slot) {
         const uint32_t last_use = (gs - 1 - slot) / p.stages;
         if (!mbar_try_wait(&full[slot], last_use & 1)) {
@@ -171,6 +173,15 @@ __device__ __forceinline__ void produce(const P &p, long long chunk, float2 *rin
             }
         }
     }
+}
+
+// One thread streams this CTA's factor chunk, stage by stage, into the ring.
+template <class P>
+__device__ __forceinline__ void produce(const P &p, long long chunk, float2 *ring, uint64_t *full, uint64_t *empty,
+                                       volatile int *abort_flag) {
+    uint32_t gs = 0;
+    produce_chunk(p, chunk, gs, ring, full, empty, abort_flag);
+    produce_drain(p, gs, full, abort_flag);
 }
 
 // ------------------------------------------------------- consumer: one stage

@@ -112,12 +112,14 @@ TC_SHAPES = [(0, 16, 16), (2, 16, 16), (4, 16, 32), (6, 32, 16), (8, 16, 16), (8
 @pytest.mark.parametrize("kmax", [None, 1])
 def test_tensor_core_path(bf, L, n0, r, kmax, monkeypatch):
     """Shapes with r and leaf multiples of 16 run batches on the tcgen05 core
-    (128 RHS per CTA, 3xTF32): ragged tiles, several tiles, and the pass
-    split forced to one slot bit per pass (kmax = 1)."""
+    (128 RHS per CTA, 3xTF32; forced here for every batch size): ragged
+    tiles, several tiles, and the pass split forced to one slot bit per pass
+    (kmax = 1).  Other shapes fall back to the CUDA-core core."""
     from bfinputs import complex_normal, synthetic_factors
     monkeypatch.setenv("BF_TC", "1")
+    monkeypatch.setenv("BF_TC_MIN", "1")      # every batch on the tensor-core core
     if kmax is not None:
-        monkeypatch.setenv("BF_WIDE_KMAX", str(kmax))
+        monkeypatch.setenv("BF_TC_KMAX", str(kmax))
     F = synthetic_factors(L, n0, r, seed=500 + L + r, dtype=np.complex64)
     plan = bf.bf_plan_create(F, nrhs_max=300)
     for nrhs in (8, 130, 300):
@@ -131,6 +133,7 @@ def test_tensor_core_path_odd_ld(bf, monkeypatch):
     """Odd leading dimension: the tensor path's global accesses stay 8-byte."""
     from bfinputs import complex_normal, synthetic_factors
     monkeypatch.setenv("BF_TC", "1")
+    monkeypatch.setenv("BF_TC_MIN", "1")
     F = synthetic_factors(8, 16, 16, seed=9, dtype=np.complex64)
     plan = bf.bf_plan_create(F, nrhs_max=64)
     g = complex_normal((40, F.N), seed=2, dtype=np.complex64)
