@@ -47,6 +47,7 @@ struct WidePass {
     bool down = true;
     int load_kind = 0, store_kind = 0;
     int a = 0, kb = 0, G = 1, ngroups = 1;
+    int Kin = 0, Nout = 0;   // tensor-core core: dense block per (node, group), Nout x Kin complex
 };
 
 // Configuration of one multi-RHS core: CUDA-core (bf_wide.cuh) or tensor-core (bf_tc.cuh).
@@ -56,7 +57,6 @@ struct WideCfg {
     int slot_len = 0;      // ring slot, complex entries
     int stages = 2;
     int nr_max = 0;        // CUDA-core: largest RHS tile
-    int dn = 0, nk = 0;    // tensor-core: accumulator columns per buffer, max unit N*K
 };
 
 // The passes of one direction: down half (leaf first), then up half.
@@ -120,6 +120,15 @@ struct Src {
         if (dtype == BF_C64) return static_cast<const float2 *>(p)[i];
         const double2 v = static_cast<const double2 *>(p)[i];
         return make_float2((float)v.x, (float)v.y);
+    }
+    inline std::complex<double> atd(long long blk, int row, int col) const {
+        const long long i = (blk * rows + row) * (long long)cols + col;
+        if (dtype == BF_C64) {
+            const float2 v = static_cast<const float2 *>(p)[i];
+            return {(double)v.x, (double)v.y};
+        }
+        const double2 v = static_cast<const double2 *>(p)[i];
+        return {v.x, v.y};
     }
 };
 
@@ -326,15 +335,46 @@ inline int host_slot_of(const WidePass &wp, int g, int j) {
     return ((g >> wp.a) << (wp.a + wp.kb)) | (j << wp.a) | (g & ((1 << wp.a) - 1));
 }
 
+// Entry (rr, k) of unit u of level lv in pass wp, chunk (node c, group g):
+// the same unit matrices as the fused path (rows = the unit's outputs, cols =
+// its inputs).  Down half: (V^L)^* and (H^l)^* forward, (U^L)^* and (G^l)^*
+// adjoint; up half the others.
+struct UnitSource {
+    const WidePass &wp;
+    const bf_plan_s &P;
+    const bf_factors &f;
+    bool use_v;
+    UnitSource(const WidePass &w, bool adjoint, const bf_plan_s &pl, const bf_factors &fa)
+        : wp(w), P(pl), f(fa), use_v(w.down != adjoint) {}
+    std::complex<double> operator()(const Level &lv, int c, int g, int u, int rr, int k) const {
+        const int L = P.L, h = P.h, m = P.m, n0 = P.n0, r = P.r;
+        if (lv.kind == bfk::LEAF_IN || lv.kind == bfk::LEAF_OUT) {
+            const Src LEAF{use_v ? f.VL : f.UL, f.dtype, n0, r};
+            const long long b = (long long)c * m + host_slot_of(wp, g, u);
+            return lv.kind == bfk::LEAF_IN ? std::conj(LEAF.atd(b, k, rr)) : LEAF.atd(b, rr, k);
+        }
+        const int t = lv.pad_, sz = 1 << t, hs = sz >> 1;
+        const int j0 = host_insert0(u, lv.s);
+        const int p0 = host_slot_of(wp, g, j0);
+        const int seg = p0 >> t;
+        const int q = host_bitrev(p0 & (hs - 1), t - 1);
+        const long long nodel = (long long)c * (m / sz) + seg;
+        const int l = L - t;
+        const Src X{use_v ? f.H[l - h] : f.G[l - h], f.dtype, r, 2 * r};
+        if (lv.kind == bfk::MERGE) {
+            const int cc = k / r, kp = k % r;
+            return std::conj(X.atd((2 * nodel + cc) * hs + q, kp, rr));
+        }
+        const int cc = rr / r, kk = rr % r;
+        return X.atd((2 * nodel + cc) * hs + q, kk, k);
+    }
+};
+
 // Packs one pass: chunk (node c, group g) = c * ngroups + g; units in the
 // order the CTA runs them; the unit matrices are the fused path's.
-void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P, const bf_factors &f, bool tc) {
-    const bool down = wp.down;   // tc: tensor-core layout, per unit one K-major operand [Re B; Im B]
-    const int L = P.L, h = P.h, m = P.m, n0 = P.n0, r = P.r;
-    const Src VL{f.VL, f.dtype, n0, r}, UL{f.UL, f.dtype, n0, r};
-    // down half reads V/H (forward) or U/G (adjoint); up half the others
-    const bool use_v = (down != adjoint);
-    const Src &LEAF = use_v ? VL : UL;
+void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P, const bf_factors &f) {
+    const int m = P.m;
+    const UnitSource unit(wp, adjoint, P, f);
     const Stream &st = wp.st;
     auto work = [&](int c0, int c1) {
         for (int c = c0; c < c1; ++c) {
@@ -346,38 +386,12 @@ void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P
                     for (int stg = 0; stg < lv.nstages; ++stg) {
                         for (int ui = 0; ui < lv.upb; ++ui) {
                             const int u = stg * lv.upb + ui;
-                            for (int rr = 0; rr < lv.rpu; ++rr) {
+                            for (int rr = 0; rr < lv.rpu; ++rr)
                                 for (int k = 0; k < lv.K; ++k) {
-                                    float2 v;
-                                    if (lv.kind == bfk::LEAF_IN || lv.kind == bfk::LEAF_OUT) {
-                                        const long long b = (long long)c * m + host_slot_of(wp, g, u);
-                                        v = lv.kind == bfk::LEAF_IN ? conjf2(LEAF.at(b, k, rr)) : LEAF.at(b, rr, k);
-                                    } else {
-                                        const int t = lv.pad_, sz = 1 << t, hs = sz >> 1;
-                                        const int j0 = host_insert0(u, lv.s);
-                                        const int p0 = host_slot_of(wp, g, j0);
-                                        const int seg = p0 >> t;
-                                        const int q = host_bitrev(p0 & (hs - 1), t - 1);
-                                        const long long nodel = (long long)c * (m / sz) + seg;
-                                        const int l = L - t;
-                                        const Src X{use_v ? f.H[l - h] : f.G[l - h], f.dtype, r, 2 * r};
-                                        if (lv.kind == bfk::MERGE) {
-                                            const int cc = k / r, kp = k % r;
-                                            v = conjf2(X.at((2 * nodel + cc) * hs + q, kp, rr));
-                                        } else {
-                                            const int cc = rr / r, kk = rr % r;
-                                            v = X.at((2 * nodel + cc) * hs + q, kk, k);
-                                        }
-                                    }
-                                    if (tc) {   // one operand of 2N rows: [Re B; Im B]
-                                        float *uf = reinterpret_cast<float *>(o) + (long long)ui * 2 * lv.rpu * lv.K;
-                                        uf[bftc::boff(rr, k, 2 * lv.rpu) >> 2] = v.x;
-                                        uf[bftc::boff(lv.rpu + rr, k, 2 * lv.rpu) >> 2] = v.y;
-                                    } else {
-                                        o[(long long)k * rows + (long long)ui * lv.rpu + rr] = v;
-                                    }
+                                    const std::complex<double> v = unit(lv, c, g, u, rr, k);
+                                    o[(long long)k * rows + (long long)ui * lv.rpu + rr] =
+                                        make_float2((float)v.real(), (float)v.imag());
                                 }
-                            }
                         }
                         if (lv.stage_len > rows * lv.K) o[lv.stage_len - 1] = make_float2(0.f, 0.f);
                         o += lv.stage_len;
@@ -394,6 +408,98 @@ void pack_wide(float2 *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P
     for (auto &th : pool) th.join();
 }
 
+// Tensor-core core: the pass's levels (and the leaf, and S^h of M^h) on one
+// group of G slots multiplied out, in FP64, into one dense block F
+// (Nout x Kin); stored per chunk as the K-major operand [Re F; Im F].
+void pack_tc(float *dst, const WidePass &wp, bool adjoint, const bf_plan_s &P, const bf_factors &f) {
+    using cd = std::complex<double>;
+    const int m = P.m, r = P.r, n0 = P.n0, G = wp.G, Kin = wp.Kin, Nout = wp.Nout;
+    const UnitSource unit(wp, adjoint, P, f);
+    const Stream &st = wp.st;
+    auto S_at = [&](long long i) -> double {
+        return f.dtype == BF_C64 ? (double)static_cast<const float *>(f.S)[i] : static_cast<const double *>(f.S)[i];
+    };
+    auto work = [&](int c0, int c1) {
+        std::vector<cd> F, T;
+        for (int c = c0; c < c1; ++c) {
+            for (int g = 0; g < wp.ngroups; ++g) {
+                int li = 0, rows;
+                if (st.lev[0].kind == bfk::LEAF_IN) {
+                    rows = G * r;
+                    F.assign((size_t)rows * Kin, cd(0));
+                    for (int j = 0; j < G; ++j)
+                        for (int rr = 0; rr < r; ++rr)
+                            for (int k = 0; k < n0; ++k)
+                                F[(size_t)(j * r + rr) * Kin + j * n0 + k] = unit(st.lev[0], c, g, j, rr, k);
+                    li = 1;
+                } else {
+                    rows = G * r;
+                    F.assign((size_t)rows * Kin, cd(0));
+                    for (int j = 0; j < G; ++j)
+                        for (int kk = 0; kk < r; ++kk) {
+                            double w = 1.0;
+                            if (wp.load_kind == bfw::LD_GATHER) {
+                                // M^h: slot ps of row node c holds logical block q = bitrev_h(ps), times S
+                                const int q = host_bitrev(host_slot_of(wp, g, j), P.h);
+                                w = adjoint ? S_at(((long long)q * m + c) * r + kk) : S_at(((long long)c * m + q) * r + kk);
+                            }
+                            F[(size_t)(j * r + kk) * Kin + j * r + kk] = w;
+                        }
+                }
+                for (; li < st.nlev; ++li) {
+                    const Level &lv = st.lev[li];
+                    if (lv.kind == bfk::LEAF_OUT) {
+                        T.assign((size_t)G * n0 * Kin, cd(0));
+                        for (int j = 0; j < G; ++j)
+                            for (int pt = 0; pt < n0; ++pt) {
+                                cd *o = &T[(size_t)(j * n0 + pt) * Kin];
+                                for (int kk = 0; kk < r; ++kk) {
+                                    const cd b = unit(lv, c, g, j, pt, kk);
+                                    const cd *x = &F[(size_t)(j * r + kk) * Kin];
+                                    for (int k = 0; k < Kin; ++k) o[k] += b * x[k];
+                                }
+                            }
+                        F.swap(T);
+                        rows = G * n0;
+                        continue;
+                    }
+                    // butterflies on slot pairs (j0, j1) differing in local bit lv.s
+                    T.assign((size_t)2 * r * Kin, cd(0));
+                    for (int u = 0; u < G / 2; ++u) {
+                        const int j0 = host_insert0(u, lv.s), j1 = j0 | (1 << lv.s);
+                        std::fill(T.begin(), T.end(), cd(0));
+                        for (int rr = 0; rr < 2 * r; ++rr) {
+                            cd *o = &T[(size_t)rr * Kin];
+                            for (int k = 0; k < 2 * r; ++k) {
+                                const cd b = unit(lv, c, g, u, rr, k);
+                                const cd *x = &F[(size_t)((k < r ? j0 : j1) * r + k % r) * Kin];
+                                for (int kx = 0; kx < Kin; ++kx) o[kx] += b * x[kx];
+                            }
+                        }
+                        for (int rr = 0; rr < 2 * r; ++rr)
+                            std::copy(&T[(size_t)rr * Kin], &T[(size_t)rr * Kin] + Kin,
+                                      &F[(size_t)((rr < r ? j0 : j1) * r + rr % r) * Kin]);
+                    }
+                }
+                float *o = dst + ((long long)c * wp.ngroups + g) * 2ll * Nout * Kin;
+                for (int rr = 0; rr < Nout; ++rr)
+                    for (int k = 0; k < Kin; ++k) {
+                        const cd v = F[(size_t)rr * Kin + k];
+                        o[bftc::boff(rr, k, 2 * Nout) >> 2] = (float)v.real();
+                        o[bftc::boff(Nout + rr, k, 2 * Nout) >> 2] = (float)v.imag();
+                    }
+                (void)rows;
+            }
+        }
+    };
+    int nthreads = (int)std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    nthreads = std::min(nthreads, m);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back(work, (int)((long long)m * t / nthreads), (int)((long long)m * (t + 1) / nthreads));
+    for (auto &th : pool) th.join();
+}
+
 bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool adjoint, const bf_factors &f, bool tc) {
     const size_t n = (size_t)P.m * wp.ngroups * wp.st.cta_len;
     std::vector<float2> host;
@@ -402,7 +508,8 @@ bf_status upload_wide(bf_plan_s &P, WidePass &wp, bool adjoint, const bf_factors
     } catch (const std::bad_alloc &) {
         return BF_ERR_NOMEM;
     }
-    pack_wide(host.data(), wp, adjoint, P, f, tc);
+    if (tc) pack_tc(reinterpret_cast<float *>(host.data()), wp, adjoint, P, f);
+    else pack_wide(host.data(), wp, adjoint, P, f);
     BF_CUDA(cudaMalloc(&wp.st.d, n * sizeof(float2)));
     P.device_bytes += n * sizeof(float2);
     BF_CUDA(cudaMemcpy(wp.st.d, host.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
@@ -438,13 +545,11 @@ long long ws_rhs(const bf_plan_s &P) {
     return P.tc ? (long long)(P.nrhs_max + bftc::NR - 1) / bftc::NR * bftc::NR : P.nrhs_max;
 }
 
-size_t tc_smem(const WideCfg &c) { return bftc::tc_smem_bytes(c.stages, c.slot_len, c.nk); }
-
 template <int NR>
 cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float *d_S, const float2 *in, long long ld_in,
                         float2 *out, long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
     const WideCfg &c = D.cfg;
-    const size_t smem = c.tc ? tc_smem(c) : wide_smem(P, c, NR);
+    const size_t smem = wide_smem(P, c, NR);
     float2 *buf[2] = {P.d_wsA, P.d_ws};
     const int np = (int)D.pass.size();
     if (tm) cudaEventRecord(tm->a, s);
@@ -454,14 +559,10 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
         std::memset(&p, 0, sizeof(p));
         p.fac = wp.st.d;
         p.cta_len = wp.st.cta_len;
-        // tensor-core core: intermediates [position][RHS] (RHS padded to the 128-row tile)
-        const long long ldt = c.tc ? (long long)(nrhs + bftc::NR - 1) / bftc::NR * bftc::NR : P.R;
         p.in = ps == 0 ? in : buf[(ps - 1) & 1];
-        p.ld_in = ps == 0 ? ld_in : ldt;
+        p.ld_in = ps == 0 ? ld_in : P.R;
         p.out = ps == np - 1 ? out : buf[ps & 1];
-        p.ld_out = ps == np - 1 ? ld_out : ldt;
-        p.in_t = c.tc && ps > 0;
-        p.out_t = c.tc && ps < np - 1;
+        p.ld_out = ps == np - 1 ? ld_out : P.R;
         p.S = d_S;
         p.err = P.d_err;
         p.nlev = wp.st.nlev;
@@ -480,18 +581,69 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
         p.stages = c.stages;
         p.slot_len = c.slot_len;
         for (int i = 0; i < wp.st.nlev; ++i) p.lev[i] = wp.st.lev[i];
-        if (c.tc) {
-            const long long items = (long long)((nrhs + bftc::NR - 1) / bftc::NR) * P.m * wp.ngroups;
-            const int grid = (int)std::min<long long>(items, P.num_sms);   // persistent: one CTA per SM
-            bftc::bf_tc_kernel<<<grid, bftc::kTcThreads, tc_smem(c), s>>>(p, c.nk, c.dn);
-        } else {
-            const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
-            bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
-        }
+        const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
+        bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
         if (tm && ps + 1 < np && !D.pass[ps + 1].down && wp.down) cudaEventRecord(tm->b, s);
     }
     if (tm) cudaEventRecord(tm->c, s);
     return cudaGetLastError();
+}
+
+// Tensor-core multi-RHS core: one persistent launch (one CTA per SM) per
+// pass; pass intermediates are stored as 128-RHS tiles [tile][position][128].
+// `in` / `out` must be 16-byte aligned with an even leading dimension.
+cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *in, long long ld_in, float2 *out,
+                      long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
+    float2 *buf[2] = {P.d_wsA, P.d_ws};
+    const int np = (int)D.pass.size();
+    const long long ntiles = (nrhs + bftc::NR - 1) / bftc::NR;
+    if (tm) cudaEventRecord(tm->a, s);
+    for (int ps = 0; ps < np; ++ps) {
+        const WidePass &wp = D.pass[ps];
+        bftc::TcParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.fac = reinterpret_cast<const float *>(wp.st.d);
+        p.in = ps == 0 ? in : buf[(ps - 1) & 1];
+        p.ld_in = ps == 0 ? ld_in : 0;
+        p.out = ps == np - 1 ? out : buf[ps & 1];
+        p.ld_out = ps == np - 1 ? ld_out : 0;
+        p.R = P.R;
+        p.err = P.d_err;
+        p.load_kind = wp.load_kind;   // bfw and bftc load kinds share their numbering
+        p.store_kind = wp.store_kind == bfw::ST_NONE ? bftc::ST_POINTS
+                     : wp.store_kind == bfw::ST_LOGICAL ? bftc::ST_LOGICAL : bftc::ST_SLOTS;
+        p.m = P.m;
+        p.r = P.r;
+        p.n0 = P.n0;
+        p.h = P.h;
+        p.a = wp.a;
+        p.kb = wp.kb;
+        p.G = wp.G;
+        p.ngroups = wp.ngroups;
+        p.Kin = wp.Kin;
+        p.Nout = wp.Nout;
+        p.nrhs = nrhs;
+        const long long items = ntiles * P.m * wp.ngroups;
+        const int grid = (int)std::min<long long>(items, P.num_sms);
+        bftc::bf_tc_kernel<<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+        if (tm && ps + 1 < np && !D.pass[ps + 1].down && wp.down) cudaEventRecord(tm->b, s);
+    }
+    if (tm) cudaEventRecord(tm->c, s);
+    return cudaGetLastError();
+}
+
+// Unit dimensions of every tensor-core pass; false if one does not fit the
+// core (Kin and Nout multiples of 16, at most 64).
+bool set_tc_dims(WideDirection &D, const bf_plan_s &P) {
+    for (auto &wp : D.pass) {
+        const int first = wp.st.lev[0].kind, last = wp.st.lev[wp.st.nlev - 1].kind;
+        wp.Kin = wp.G * (first == bfk::LEAF_IN ? P.n0 : P.r);
+        wp.Nout = wp.G * (last == bfk::LEAF_OUT ? P.n0 : P.r);
+        wp.st.cta_len = (long long)wp.Nout * wp.Kin;   // complex entries per chunk
+        for (int d : {wp.Kin, wp.Nout})
+            if (d % 16 != 0 || d > bftc::kMaxDim) return false;
+    }
+    return true;
 }
 
 size_t plan_smem(const bf_plan_s &P, int T) { return bfk::smem_bytes(P.stages, P.slot_len, P.m, P.W, T); }
@@ -630,8 +782,32 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         Timing *tm = next_timing(*P);
         cudaError_t e;
         if (P->tc && nc >= P->tc_min) {
-            // tensor-core multi-RHS core (128 RHS per CTA)
-            e = launch_wide<64>(*P, adjoint ? P->tadj : P->tfwd, D.d_S, src, ld_in, kdst, ld_out, nc, s, tm);
+            // tensor-core multi-RHS core (128 RHS per work item).  Its TMA row
+            // copies and 16-byte stores need aligned vectors with an even leading
+            // dimension; others go through the (aligned) staging buffers.
+            auto aligned = [](const void *q, long long l) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0 && (l & 1) == 0; };
+            if (!aligned(src, ld_in) || !aligned(kdst, ld_out)) {
+                if (!P->d_stage_in) {
+                    const size_t bytes = (size_t)P->N * P->nrhs_max * sizeof(float2);
+                    BF_CUDA(cudaMalloc(&P->d_stage_in, bytes));
+                    BF_CUDA(cudaMalloc(&P->d_stage_out, bytes));
+                    P->device_bytes += 2 * bytes;
+                }
+                if (!aligned(src, ld_in)) {
+                    BF_CUDA(cudaMemcpy2DAsync(P->d_stage_in, P->N * 8, src, ld_in * 8, P->N * 8, nc,
+                                              cudaMemcpyDeviceToDevice, s));
+                    src = P->d_stage_in;
+                    ld_in = P->N;
+                }
+            }
+            if (!aligned(kdst, ld_out)) {
+                e = launch_tc(*P, adjoint ? P->tadj : P->tfwd, src, ld_in, P->d_stage_out, P->N, nc, s, tm);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(kdst, ld_out * 8, P->d_stage_out, P->N * 8, P->N * 8, nc,
+                                          cudaMemcpyDeviceToDevice, s);
+            } else {
+                e = launch_tc(*P, adjoint ? P->tadj : P->tfwd, src, ld_in, kdst, ld_out, nc, s, tm);
+            }
         } else if (P->wide && nc >= P->wide_min) {
             // CUDA-core multi-RHS core: RHS tile = smallest of 16/32/64 covering nc, capped by the plan
             const WideDirection &WD = adjoint ? P->wadj : P->wfwd;
@@ -800,25 +976,26 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
             make_wide_passes(P->wadj, *P, c);
         }
     }
-    if (P->nrhs_max >= std::max(P->tc_min, 1) && env_int("BF_TC", 1) == 1 && r % 16 == 0 && n0 % 16 == 0) {
+    if (P->nrhs_max >= std::max(P->tc_min, 1) && env_int("BF_TC", 1) == 1) {
+        // Groups of G = 4 slots (two levels per pass) when the dense blocks fit
+        // (G max(n0, r) <= 64), else G = 2 or 1; BF_TC_KMAX caps the slot bits.
+        int kb = 2;
+        while (kb > 0 && (1 << kb) * std::max(n0, r) > bftc::kMaxDim) --kb;
         WideCfg c;
         c.tc = true;
-        c.dn = 2 * std::max(2 * r, n0);
-        c.nk = std::max(4 * r * r, n0 * r);
-        c.slot_len = std::max(2048, c.nk);
-        c.stages = 3;
-        // group size: as many slot bits as the tensor-memory tile allows
-        int kb = 0;
-        while (kb < std::max(P->h, 1) && bftc::tc_tmem_fits((1 << (kb + 1)) * P->W, c.dn)) ++kb;
-        c.kmax = std::min(env_int("BF_TC_KMAX", kb), kb);
-        c.nr_max = bftc::NR;
-        if (kb >= 1 && tc_smem(c) <= (size_t)kMaxSmem) {
+        c.kmax = std::max(1, std::min(env_int("BF_TC_KMAX", kb), std::max(kb, 1)));
+        c.slot_len = 1 << 30;   // unused: one dense block per chunk
+        make_wide_passes(P->tfwd, *P, c);
+        make_wide_passes(P->tadj, *P, c);
+        const bool fits = (1 << std::min(c.kmax, std::max(P->h, 0))) * std::max(n0, r) <= bftc::kMaxDim;
+        if (fits && set_tc_dims(P->tfwd, *P) && set_tc_dims(P->tadj, *P)) {
             P->tc = true;
             if (cudaFuncSetAttribute(bftc::bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)tc_smem(c)) != cudaSuccess)
+                                     (int)bftc::kSmemBytes) != cudaSuccess)
                 return fail(cuda_fail(cudaErrorInvalidValue));
-            make_wide_passes(P->tfwd, *P, c);
-            make_wide_passes(P->tadj, *P, c);
+        } else {
+            P->tfwd.pass.clear();
+            P->tadj.pass.clear();
         }
     }
     for (auto *D : {&P->wfwd, &P->wadj, &P->tfwd, &P->tadj}) {

@@ -105,16 +105,18 @@ def test_multi_rhs_path_ld_and_fio(bf):
     plan.destroy()
 
 
-TC_SHAPES = [(0, 16, 16), (2, 16, 16), (4, 16, 32), (6, 32, 16), (8, 16, 16), (8, 64, 16), (10, 16, 16)]
+TC_SHAPES = [(0, 16, 16), (2, 16, 16), (4, 16, 32), (6, 32, 16), (8, 16, 16), (8, 64, 16), (10, 16, 16),
+             (4, 8, 16), (6, 16, 8), (2, 8, 8)]
 
 
 @pytest.mark.parametrize("L,n0,r", TC_SHAPES)
 @pytest.mark.parametrize("kmax", [None, 1])
 def test_tensor_core_path(bf, L, n0, r, kmax, monkeypatch):
-    """Shapes with r and leaf multiples of 16 run batches on the tcgen05 core
-    (128 RHS per CTA, 3xTF32; forced here for every batch size): ragged
-    tiles, several tiles, and the pass split forced to one slot bit per pass
-    (kmax = 1).  Other shapes fall back to the CUDA-core core."""
+    """Batches on the tcgen05 core (dense per-group blocks, 128 RHS per work
+    item, 3xTF32; forced here for every batch size): groups of 1, 2 and 4
+    slots, ragged RHS tiles, several tiles, and one slot bit per pass
+    (kmax = 1).  Shapes whose blocks exceed 64 x 64 (n0 = 64) fall back to
+    the CUDA-core core."""
     from bfinputs import complex_normal, synthetic_factors
     monkeypatch.setenv("BF_TC", "1")
     monkeypatch.setenv("BF_TC_MIN", "1")      # every batch on the tensor-core core
@@ -130,7 +132,8 @@ def test_tensor_core_path(bf, L, n0, r, kmax, monkeypatch):
 
 
 def test_tensor_core_path_odd_ld(bf, monkeypatch):
-    """Odd leading dimension: the tensor path's global accesses stay 8-byte."""
+    """Odd leading dimension: the tensor-core core's 16-byte row copies need an
+    even one, so the call goes through aligned staging buffers."""
     from bfinputs import complex_normal, synthetic_factors
     monkeypatch.setenv("BF_TC", "1")
     monkeypatch.setenv("BF_TC_MIN", "1")
