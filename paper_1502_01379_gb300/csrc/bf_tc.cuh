@@ -38,10 +38,15 @@
 //    (one copy per slot for pass intermediates, one per RHS row for the
 //    input vectors), so HBM reads for item i+1 overlap item i's MMAs;
 //  * prep warp: F_lo for each ring slot;
-//  * MMA warp: one thread issues the item's 6 Kin/8 MMAs and commits them;
-//  * eight epilogue warps (two per tensor-memory lane quarter): read item
-//    i-1's accumulators, combine and store its outputs to global memory,
-//    then convert item i's staged tile into X and X_lo in tensor memory.
+//  * MMA warp: one thread issues the item's MMAs in two groups, first the
+//    3 Kin/8 that accumulate D (they read Re X, Re X_lo), then the 3 Kin/8
+//    for E (Im X, Im X_lo), and commits each group;
+//  * eight epilogue warps (two per tensor-memory lane quarter).  While the
+//    E group of item i-1 runs they read item i-1's D into registers and
+//    convert the real part of item i's staged tile into Re X, Re X_lo; while
+//    the D group of item i runs they read item i-1's E, combine and store its
+//    outputs, and convert the imaginary part.  So the tensor pipe does not
+//    wait for the epilogue.
 // They meet on mbarriers; every wait is bounded (bf_kernels.cuh), and on
 // expiry the CTA runs its remaining control flow without waiting or
 // computing and the producer drains the copies it issued.
@@ -64,7 +69,8 @@ constexpr int kStages = 2;
 constexpr uint32_t kSlotBytes = 2u * kMaxDim * kMaxDim * 4u;                  // 32 KB
 constexpr uint32_t kPointRow = kMaxDim * 8u + 16u;                           // padded staging row
 constexpr uint32_t kStageBytes = (uint32_t)NR * kPointRow;                   // >= Kin * NR * 8
-constexpr size_t kSmemBytes = 2ull * kStages * kSlotBytes + kStageBytes + 256;
+constexpr uint32_t kTrBytes = 32u * 64u;                                     // per-warp transpose tile
+constexpr size_t kSmemBytes = 2ull * kStages * kSlotBytes + kStageBytes + kEpiWarps * kTrBytes + 256;
 
 enum LoadKind : int { LD_POINTS = 0, LD_SLOTS = 1, LD_GATHER = 2 };
 enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2 };
@@ -121,29 +127,22 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Four 32x32b.x8 tensor-memory loads and their wait in one asm statement, so
+// Two 32x32b.x8 tensor-memory loads and their wait in one asm statement, so
 // no register is read before the data has arrived.
-__device__ __forceinline__ void tmem_ld8x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, float (&v0)[8],
-                                           float (&v1)[8], float (&v2)[8], float (&v3)[8]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld8x2(uint32_t a0, uint32_t a1, float (&v0)[8], float (&v1)[8]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(a0), "r"(a1)
         : "memory");
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         v0[i] = __uint_as_float(r[i]);
         v1[i] = __uint_as_float(r[8 + i]);
-        v2[i] = __uint_as_float(r[16 + i]);
-        v3[i] = __uint_as_float(r[24 + i]);
     }
 }
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
@@ -160,8 +159,11 @@ __device__ __forceinline__ float lo_part(float x) { return x - __uint_as_float(_
 struct Smem {
     float *ring, *blo;                 // kStages slots of kSlotBytes each
     unsigned char *xs;                 // input staging
+    float4 *tr;                        // per-warp transpose tiles (output rows)
     uint64_t *full, *empty, *bready;   // [kStages]
-    uint64_t *xfull, *xfree, *xready, *dfull;
+    uint64_t *xfull, *xfree;           // staging landed / consumed
+    uint64_t *xrready, *xiready;       // Re X / Im X written (and D / E of the last item read)
+    uint64_t *ddone, *edone;           // D group / E group of MMAs completed
     uint32_t *tmem_slot;
     volatile int *abort_flag;
 };
@@ -273,100 +275,130 @@ __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitem
     }
 }
 
-// MMA warp (one thread): the item's 6 Kin/8 MMAs into D and E.
+// MMA warp (one thread): per item the D group (Re X) then the E group (Im X).
 __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uint32_t tmem, int nitems) {
     const int rows = 2 * p.Nout;
     const uint32_t lbo = (uint32_t)(rows >> 3) * 128u;
     const uint32_t idesc = idesc_tf32(rows);
-    const uint32_t d = tmem + kD, e = tmem + kE;
     uint32_t it = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
         const uint32_t slot = it % kStages;
-        bool ok = !*s.abort_flag && bfk::mbar_wait(s.xready, it & 1, s.abort_flag, p.err);
+        const uint32_t b1 = bfk::smem_u32(s.ring) + slot * kSlotBytes;
+        const uint32_t bl = bfk::smem_u32(s.blo) + slot * kSlotBytes;
+        bool ok = !*s.abort_flag && bfk::mbar_wait(s.xrready, it & 1, s.abort_flag, p.err);
         ok = ok && bfk::mbar_wait(&s.bready[slot], (it / kStages) & 1, s.abort_flag, p.err);
         tc_fence_after();
-        if (ok) {
-            const uint32_t b1 = bfk::smem_u32(s.ring) + slot * kSlotBytes;
-            const uint32_t bl = bfk::smem_u32(s.blo) + slot * kSlotBytes;
-            for (int kk = 0; kk < p.Kin / 8; ++kk) {
-                const uint32_t bo = (uint32_t)(2 * kk) * lbo;
-                const uint64_t B = sdesc(b1 + bo, lbo, 128), Bl = sdesc(bl + bo, lbo, 128);
-                const uint32_t c = (uint32_t)(8 * kk);
-                const uint32_t acc = kk > 0 ? 1u : 0u;
-                mma_ts(d, tmem + kXr + c, B, idesc, acc);
-                mma_ts(d, tmem + kXr + c, Bl, idesc, 1);
-                mma_ts(d, tmem + kXrl + c, B, idesc, 1);
-                mma_ts(e, tmem + kXi + c, B, idesc, acc);
-                mma_ts(e, tmem + kXi + c, Bl, idesc, 1);
-                mma_ts(e, tmem + kXil + c, B, idesc, 1);
+        for (int grp = 0; grp < 2; ++grp) {
+            if (grp == 1) {
+                ok = ok && bfk::mbar_wait(s.xiready, it & 1, s.abort_flag, p.err);
+                tc_fence_after();
             }
+            const uint32_t d = tmem + (grp ? kE : kD);
+            const uint32_t xh = tmem + (grp ? kXi : kXr), xl = tmem + (grp ? kXil : kXrl);
+            if (ok) {
+                for (int kk = 0; kk < p.Kin / 8; ++kk) {
+                    const uint32_t bo = (uint32_t)(2 * kk) * lbo;
+                    const uint64_t B = sdesc(b1 + bo, lbo, 128), Bl = sdesc(bl + bo, lbo, 128);
+                    const uint32_t c = (uint32_t)(8 * kk);
+                    mma_ts(d, xh + c, B, idesc, kk > 0 ? 1u : 0u);
+                    mma_ts(d, xh + c, Bl, idesc, 1);
+                    mma_ts(d, xl + c, B, idesc, 1);
+                }
+            }
+            if (grp == 1) mma_commit(&s.empty[slot]);   // ring slot and F_lo free once both groups completed
+            mma_commit(grp ? s.edone : s.ddone);
         }
-        mma_commit(&s.empty[slot]);   // ring slot and F_lo free once these MMAs completed
-        mma_commit(s.dfull);
     }
-    if (it > 0) drain_wait(s.dfull, (it - 1) & 1);   // no MMA in flight when tensor memory is freed
+    if (it > 0) drain_wait(s.edone, (it - 1) & 1);   // no MMA in flight when tensor memory is freed
 }
 
-// Staged input tile -> X and X_lo in tensor memory (this thread's RHS lane,
-// positions of its half).
-__device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32_t lb, int mlane, int hf) {
+// One part (0 = real, 1 = imaginary) of the staged input tile -> X and X_lo
+// in tensor memory (this thread's RHS lane, positions of its half).
+__device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32_t lb, int mlane, int hf, int part) {
     const int half = p.Kin >> 1;
+    const uint32_t ch = part ? kXi : kXr, cl = part ? kXil : kXrl;
     for (int e = hf * half; e < (hf + 1) * half; e += 8) {
-        float re[8], im[8], rl[8], il[8];
+        float v[8], vl[8];
         if (p.load_kind == LD_POINTS) {
             const float4 *row = reinterpret_cast<const float4 *>(s.xs + (size_t)mlane * kPointRow) + (e >> 1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float4 v = row[i];
-                re[2 * i] = v.x;
-                im[2 * i] = v.y;
-                re[2 * i + 1] = v.z;
-                im[2 * i + 1] = v.w;
+                const float4 q = row[i];
+                v[2 * i] = part ? q.y : q.x;
+                v[2 * i + 1] = part ? q.w : q.z;
             }
         } else {
-            const float2 *col = reinterpret_cast<const float2 *>(s.xs) + (size_t)e * NR + mlane;
+            const float *col = reinterpret_cast<const float *>(s.xs) + ((size_t)e * NR + mlane) * 2 + part;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float2 v = col[(size_t)i * NR];
-                re[i] = v.x;
-                im[i] = v.y;
-            }
+            for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * NR * 2];
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            rl[i] = lo_part(re[i]);
-            il[i] = lo_part(im[i]);
-        }
-        tmem_st8(lb + kXr + (uint32_t)e, re);
-        tmem_st8(lb + kXi + (uint32_t)e, im);
-        tmem_st8(lb + kXrl + (uint32_t)e, rl);
-        tmem_st8(lb + kXil + (uint32_t)e, il);
+        for (int i = 0; i < 8; ++i) vl[i] = lo_part(v[i]);
+        tmem_st8(lb + ch + (uint32_t)e, v);
+        tmem_st8(lb + cl + (uint32_t)e, vl);
     }
     tmem_wait_st();
 }
 
-// Item's accumulators -> outputs (this thread's RHS lane, outputs of its half).
-__device__ __forceinline__ void epilogue(const TcParams &p, const Item &w, uint32_t lb, int mlane, int hf) {
+// Accumulator registers of one thread: its Nout/2 <= 32 outputs, chunks of 8.
+struct Acc {
+    float re[4][8], im[4][8];
+};
+
+// D of the item -> registers (D[:, o] into re, D[:, Nout+o] into im).
+__device__ __forceinline__ void read_d(const TcParams &p, uint32_t lb, int hf, Acc &a) {
+    const int half = p.Nout >> 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int o = hf * half + 8 * c;
+        if (8 * c < half) tmem_ld8x2(lb + kD + (uint32_t)o, lb + kD + (uint32_t)(p.Nout + o), a.re[c], a.im[c]);
+    }
+}
+
+// Stores 8 consecutive outputs of this thread's RHS row (ST_POINTS) through
+// the warp's transpose tile: each lane writes its 64-byte row segment, then
+// each store instruction writes eight rows' 64-byte segments (whole sectors).
+// The tile's 16-byte chunks are XOR-swizzled so both phases are conflict-free.
+__device__ __forceinline__ void store_points8(const TcParams &p, const Smem &s, const Item &w, int q, int o,
+                                              const float (&re)[8], const float (&im)[8]) {
+    const int lane = threadIdx.x & 31;
+    float4 *tr = s.tr + (size_t)(threadIdx.x >> 5) * (kTrBytes / 16);
+    const int sw = (lane >> 1) & 3;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tr[lane * 4 + (c ^ sw)] = make_float4(re[2 * c], im[2 * c], re[2 * c + 1], im[2 * c + 1]);
+    __syncwarp();
+    const int j = o / p.n0, pt = o - j * p.n0;
+    const long long col = ((long long)w.n * p.m + slot_of(p, w.g, j)) * p.n0 + pt;   // first of the 8 points
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const int row = 8 * st + (lane >> 2), c = lane & 3;
+        const float4 v = tr[row * 4 + (c ^ ((row >> 1) & 3))];
+        if (q * 32 + row < w.nt)
+            *reinterpret_cast<float4 *>(p.out + (long long)(w.t * NR + q * 32 + row) * p.ld_out + col + 2 * c) = v;
+    }
+    __syncwarp();
+}
+
+// E of the item, combined with its D (registers) into outputs, stored.
+__device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const Item &w, uint32_t lb, int q, int mlane,
+                                       int hf, Acc &a) {
     const int half = p.Nout >> 1;
     const bool live = mlane < w.nt;
-    for (int o = hf * half; o < (hf + 1) * half; o += 8) {
-        float dr[8], di[8], er[8], ei[8];
-        tmem_ld8x4(lb + kD + (uint32_t)o, lb + kD + (uint32_t)(p.Nout + o), lb + kE + (uint32_t)o,
-                   lb + kE + (uint32_t)(p.Nout + o), dr, di, er, ei);
-        if (!live) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (8 * c >= half) continue;
+        const int o = hf * half + 8 * c;
+        float er[8], ei[8];
+        tmem_ld8x2(lb + kE + (uint32_t)o, lb + kE + (uint32_t)(p.Nout + o), er, ei);
         float re[8], im[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            re[i] = dr[i] - ei[i];
-            im[i] = di[i] + er[i];
+            re[i] = a.re[c][i] - ei[i];
+            im[i] = a.im[c][i] + er[i];
         }
         if (p.store_kind == ST_POINTS) {
-            const int j = o / p.n0, pt = o - j * p.n0;
-            float4 *dst = reinterpret_cast<float4 *>(p.out + (long long)(w.t * NR + mlane) * p.ld_out +
-                                                     ((long long)w.n * p.m + slot_of(p, w.g, j)) * p.n0 + pt);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
-        } else {
+            store_points8(p, s, w, q, o, re, im);
+        } else if (live) {
             const int j = o / p.r, kk = o - j * p.r;
             const int ps = slot_of(p, w.g, j);
             const int blk = p.store_kind == ST_LOGICAL ? bitrev(ps, p.h) : ps;
@@ -383,15 +415,18 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const TcParams p) {
     s.ring = reinterpret_cast<float *>(smem_raw);
     s.blo = s.ring + (size_t)kStages * (kSlotBytes / 4);
     s.xs = reinterpret_cast<unsigned char *>(s.blo + (size_t)kStages * (kSlotBytes / 4));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s.xs + kStageBytes);
+    s.tr = reinterpret_cast<float4 *>(s.xs + kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s.xs + kStageBytes + kEpiWarps * kTrBytes);
     s.full = bars;
     s.empty = bars + kStages;
     s.bready = bars + 2 * kStages;
     s.xfull = bars + 3 * kStages;
     s.xfree = s.xfull + 1;
-    s.xready = s.xfull + 2;
-    s.dfull = s.xfull + 3;
-    s.tmem_slot = reinterpret_cast<uint32_t *>(s.xfull + 4);
+    s.xrready = s.xfull + 2;
+    s.xiready = s.xfull + 3;
+    s.ddone = s.xfull + 4;
+    s.edone = s.xfull + 5;
+    s.tmem_slot = reinterpret_cast<uint32_t *>(s.xfull + 6);
     s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
@@ -402,8 +437,10 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const TcParams p) {
         }
         bfk::mbar_init(s.xfull, 1);
         bfk::mbar_init(s.xfree, kEpiWarps);
-        bfk::mbar_init(s.xready, kEpiWarps);
-        bfk::mbar_init(s.dfull, 1);
+        bfk::mbar_init(s.xrready, kEpiWarps);
+        bfk::mbar_init(s.xiready, kEpiWarps);
+        bfk::mbar_init(s.ddone, 1);
+        bfk::mbar_init(s.edone, 1);
         *s.abort_flag = 0;
         bfk::fence_mbar_init();
     }
@@ -432,23 +469,37 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const TcParams p) {
         const uint32_t lb = tmem + ((uint32_t)(q * 32) << 16);
         uint32_t it = 0;
         Item prev{};
+        Acc acc;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
-            if (it > 0) {
-                const bool ok = warp_wait(s.dfull, (it - 1) & 1, s.abort_flag, p.err);
-                tc_fence_after();
-                if (ok) epilogue(p, prev, lb, mlane, hf);
-            }
             const Item w = decode(p, item, ntiles);
-            if (warp_wait(s.xfull, it & 1, s.abort_flag, p.err)) convert(p, s, lb, mlane, hf);
+            bool okd = false;
+            if (it > 0) {   // item it-1: D -> registers (its E group is running)
+                okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
+                tc_fence_after();
+                if (okd) read_d(p, lb, hf, acc);
+            }
+            const bool okx = warp_wait(s.xfull, it & 1, s.abort_flag, p.err);
+            if (okx) convert(p, s, lb, mlane, hf, 0);
             tc_fence_before();
+            warp_arrive(s.xrready);
+            if (it > 0) {   // item it-1: E, combine, store (item it's D group is running)
+                const bool oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
+                tc_fence_after();
+                if (okd && oke) finish(p, s, prev, lb, q, mlane, hf, acc);
+            }
+            if (okx) convert(p, s, lb, mlane, hf, 1);
+            tc_fence_before();
+            warp_arrive(s.xiready);
             warp_arrive(s.xfree);
-            warp_arrive(s.xready);
             prev = w;
         }
         if (it > 0) {
-            const bool ok = warp_wait(s.dfull, (it - 1) & 1, s.abort_flag, p.err);
+            const bool okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
             tc_fence_after();
-            if (ok) epilogue(p, prev, lb, mlane, hf);
+            if (okd) read_d(p, lb, hf, acc);
+            const bool oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
+            tc_fence_after();
+            if (okd && oke) finish(p, s, prev, lb, q, mlane, hf, acc);
         }
     }
     tc_fence_before();
