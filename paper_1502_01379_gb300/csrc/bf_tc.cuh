@@ -31,12 +31,19 @@
 // Tensor memory (512 columns): Re X | Im X | Re X_lo | Im X_lo (64 each) |
 // D (128) | E (128).
 //
+// Pass intermediates are 128-RHS tiles stored position-major and planar:
+// position pos of tile t holds the 128 real parts, then the 128 imaginary
+// parts (1 KB), so an r-block is one contiguous copy and each warp access to
+// one part of one position is 128 contiguous bytes.
+//
 // Warp roles (one persistent CTA per SM, looping over work items
 // (node, group, 128-RHS tile)):
 //  * producer warp: TMA bulk copies of each item's block F into a two-slot
 //    ring and of the item's input tile into a shared-memory staging buffer
 //    (one copy per slot for pass intermediates, one per RHS row for the
-//    input vectors), so HBM reads for item i+1 overlap item i's MMAs;
+//    input vectors); when it issues item i's copies it also prefetches item
+//    i+1's block and tile into L2, so the staging copy of item i+1 (issued
+//    once item i's tile is converted) reads from L2;
 //  * prep warp: F_lo for each ring slot;
 //  * MMA warp: one thread issues the item's MMAs in two groups, first the
 //    3 Kin/8 that accumulate D (they read Re X, Re X_lo), then the 3 Kin/8
@@ -77,9 +84,9 @@ enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2 };
 
 struct TcParams {
     const float *fac;       // per (node, group): [Re F; Im F], 2 Nout x Kin, K-major no-swizzle
-    const float2 *in;       // LD_POINTS: vectors, RHS j at in + j ld_in; else tiles [t][R][128]
+    const float2 *in;       // LD_POINTS: vectors, RHS j at in + j ld_in; else tiles [t][R][re 128 | im 128]
     long long ld_in;
-    float2 *out;            // ST_POINTS: vectors, RHS j at out + j ld_out; else tiles [t][R][128]
+    float2 *out;            // ST_POINTS: vectors, RHS j at out + j ld_out; else tiles [t][R][re 128 | im 128]
     long long ld_out;
     long long R;            // positions per RHS in an intermediate (2^L r)
     unsigned *err;
@@ -199,6 +206,10 @@ __device__ __forceinline__ long long slot_pos(const TcParams &p, const Item &it,
     return ((long long)it.n * p.m + ps) * p.r;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bounded wait that ignores the abort flag (drains before exit).
 __device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity) {
     if (bfk::mbar_try_wait(bar, parity)) return;
@@ -207,45 +218,58 @@ __device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
+// Global sources of an item's block F and input tile: `fn(src, bytes)` per copy,
+// the tile's copies distributed over the warp's lanes.
+template <class Fn>
+__device__ __forceinline__ void tile_copies(const TcParams &p, const Item &w, int lane, Fn fn) {
+    if (p.load_kind == LD_POINTS) {
+        const float2 *src = p.in + (long long)(w.t * NR) * p.ld_in + ((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0;
+        for (int row = lane; row < w.nt; row += 32) fn(row, src + (long long)row * p.ld_in, (uint32_t)p.Kin * 8u);
+    } else {
+        for (int j = lane; j < p.G; j += 32)
+            fn(j, p.in + ((long long)w.t * p.R + slot_pos(p, w, j)) * NR, (uint32_t)p.r * NR * 8u);
+    }
+}
+__device__ __forceinline__ uint32_t tile_bytes(const TcParams &p, const Item &w) {
+    return p.load_kind == LD_POINTS ? (uint32_t)p.Kin * 8u * (uint32_t)w.nt : (uint32_t)p.r * NR * 8u * (uint32_t)p.G;
+}
+__device__ __forceinline__ const float *block_src(const TcParams &p, const Item &w) {
+    return p.fac + ((long long)w.n * p.ngroups + w.g) * (2ll * p.Nout * p.Kin);
+}
+
 // Producer warp: the item's block F into ring slot (it % kStages), then its
 // input tile into the staging buffer once the epilogue warps have converted
-// the previous one.
+// the previous one; with the copies of item i, L2 prefetches of item i+1.
 __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int ntiles, int nitems) {
     const int lane = threadIdx.x & 31;
     const uint32_t ubytes = 2u * p.Nout * p.Kin * 4u;
     uint32_t nf = 0, nx = 0;   // factor copies / staging groups issued
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const Item w = decode(p, item, ntiles);
-        const long long ng = (long long)w.n * p.ngroups + w.g;
         const uint32_t slot = nf % kStages, use = nf / kStages;
         bool ok = true;
         if (lane == 0) {
             ok = !*s.abort_flag && (use == 0 || bfk::mbar_wait(&s.empty[slot], (use - 1) & 1, s.abort_flag, p.err));
             if (ok) {
                 bfk::mbar_arrive_expect_tx(&s.full[slot], ubytes);
-                bfk::bulk_g2s(s.ring + (size_t)slot * (kSlotBytes / 4), p.fac + ng * (2ll * p.Nout * p.Kin), ubytes,
-                              &s.full[slot]);
+                bfk::bulk_g2s(s.ring + (size_t)slot * (kSlotBytes / 4), block_src(p, w), ubytes, &s.full[slot]);
             }
         }
         if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0) == 0) break;
         ++nf;
         if (nx > 0 && !warp_wait(s.xfree, (nx - 1) & 1, s.abort_flag, p.err)) break;
-        if (p.load_kind == LD_POINTS) {
-            const uint32_t rowb = (uint32_t)p.Kin * 8u;
-            if (lane == 0) bfk::mbar_arrive_expect_tx(s.xfull, rowb * (uint32_t)w.nt);
-            __syncwarp();
-            const float2 *src = p.in + (long long)(w.t * NR) * p.ld_in + ((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0;
-            for (int row = lane; row < w.nt; row += 32)
-                bfk::bulk_g2s(s.xs + (size_t)row * kPointRow, src + (long long)row * p.ld_in, rowb, s.xfull);
-        } else {
-            const uint32_t slotb = (uint32_t)p.r * NR * 8u;
-            if (lane == 0) bfk::mbar_arrive_expect_tx(s.xfull, slotb * (uint32_t)p.G);
-            __syncwarp();
-            for (int j = lane; j < p.G; j += 32)
-                bfk::bulk_g2s(s.xs + (size_t)j * slotb, p.in + ((long long)w.t * p.R + slot_pos(p, w, j)) * NR, slotb,
-                              s.xfull);
-        }
+        if (lane == 0) bfk::mbar_arrive_expect_tx(s.xfull, tile_bytes(p, w));
+        __syncwarp();
+        if (p.load_kind == LD_POINTS)
+            tile_copies(p, w, lane, [&](int i, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + (size_t)i * kPointRow, src, b, s.xfull); });
+        else
+            tile_copies(p, w, lane, [&](int i, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + (size_t)i * b, src, b, s.xfull); });
         ++nx;
+        if (item + (int)gridDim.x < nitems) {   // next item of this CTA: into L2
+            const Item w2 = decode(p, item + gridDim.x, ntiles);
+            if (lane == 0) prefetch_l2(block_src(p, w2), ubytes);
+            tile_copies(p, w2, lane, [&](int, const void *src, uint32_t b) { prefetch_l2(src, b); });
+        }
     }
     // Every copy issued must land before the CTA may exit.
     if (lane == 0) {
@@ -328,9 +352,9 @@ __device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32
                 v[2 * i + 1] = part ? q.w : q.z;
             }
         } else {
-            const float *col = reinterpret_cast<const float *>(s.xs) + ((size_t)e * NR + mlane) * 2 + part;
+            const float *col = reinterpret_cast<const float *>(s.xs) + (size_t)e * 2 * NR + part * NR + mlane;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * NR * 2];
+            for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * 2 * NR];
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) vl[i] = lo_part(v[i]);
@@ -402,9 +426,13 @@ __device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const I
             const int j = o / p.r, kk = o - j * p.r;
             const int ps = slot_of(p, w.g, j);
             const int blk = p.store_kind == ST_LOGICAL ? bitrev(ps, p.h) : ps;
-            float2 *dst = p.out + ((long long)w.t * p.R + ((long long)w.n * p.m + blk) * p.r + kk) * NR + mlane;
+            float *dst = reinterpret_cast<float *>(p.out) +
+                         ((long long)w.t * p.R + ((long long)w.n * p.m + blk) * p.r + kk) * 2 * NR + mlane;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) dst[(size_t)i * NR] = make_float2(re[i], im[i]);
+            for (int i = 0; i < 8; ++i) {
+                dst[(size_t)i * 2 * NR] = re[i];
+                dst[(size_t)i * 2 * NR + NR] = im[i];
+            }
         }
     }
 }
