@@ -43,7 +43,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="fio_n1m_r16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--sweep", default="8,64,256", help="extra nrhs values reported in nrhs_sweep ('' = none)")
+    ap.add_argument("--sweep", default="8,32,64,128,256", help="extra nrhs values reported in nrhs_sweep ('' = none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args(argv)
@@ -255,15 +255,31 @@ def run_ours(args, rank, world, local):
     steps_e2e = max(3, args.steps // 2)
     e2e_value, _ = aggregate([ms_e2e], [2 * nrhs * steps_e2e * world])
 
-    # ---- nrhs sweep (same plan)
+    # ---- nrhs sweep (same plan); batches of >= 32 RHS run on the tensor-core core
+    tf32_peak, tf32_src = tf32_peak_tflops()
     sweep_out = []
     for n in sweep:
         gs = batch(n, 2000 + n)
         us, vs = torch.empty_like(gs), torch.empty_like(gs)
         st = 5
-        ms_s, _ = timed(gs, us, vs, n, st, 3)
+        ms_s, kt_s = timed(gs, us, vs, n, st, 3, profile=True)
         val, _ = aggregate([ms_s], [2 * n * st * world])
-        sweep_out.append({"nrhs": n, "vectors_per_s": val, "ms_per_step": ms_s / st})
+        ent = {"nrhs": n, "vectors_per_s": val, "ms_per_step": ms_s / st}
+        if n >= 32 and tc_eligible(F):
+            # per apply: kernel time of the launches (CUDA events on the stream)
+            launches = kt_s["down"][0]
+            apply_s = (kt_s["down"][1] + kt_s["up"][1]) / launches / 1e3
+            useful = 8.0 * n * apply_macs(F)
+            issued = tc_issued_flops(F, n)
+            ent["tensor"] = {
+                "kernel": "bf_tc_kernel", "apply_ms": apply_s * 1e3,
+                "useful_tflops": useful / apply_s / 1e12, "issued_tflops": issued / apply_s / 1e12,
+                "peak_tf32_tflops": tf32_peak, "peak_source": tf32_src,
+                "frac_issued": issued / apply_s / 1e12 / tf32_peak, "frac_useful": useful / apply_s / 1e12 / tf32_peak,
+                "note": "useful = 8 real flops per complex multiply-add of the factored operator; issued = "
+                        "the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi, Re and Im accumulators) of the dense per-group "
+                        "blocks; TF32 peak = measured bf16 dense peak x 1.1/2.25 (nominal TF32/BF16)"}
+        sweep_out.append(ent)
         del gs, us, vs
 
     out = {
@@ -284,6 +300,55 @@ def run_ours(args, rank, world, local):
         out["cpu_baseline"] = cpu_baseline(F, g[0].cpu().numpy(), u[0].cpu().numpy(), args.cpu_seconds)
     plan.destroy()
     return out
+
+
+def tf32_peak_tflops():
+    """TF32 dense peak: the measured bf16 burst peak x the nominal TF32/BF16 ratio (1.1 / 2.25)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
+
+
+def apply_macs(F):
+    """Complex multiply-adds of one apply per RHS: every factor entry once
+    (two leaf factors of 2^L blocks n0 x r, 2h transfer levels of 2^L blocks r x 2r)."""
+    nb = 1 << F.L
+    return 2 * nb * F.n0 * F.r + 2 * F.h * nb * 2 * F.r * F.r
+
+
+def _tc_group_bits(n0, r):
+    kb = 2
+    while kb > 0 and (1 << kb) * max(n0, r) > 64:
+        kb -= 1
+    return max(kb, 1)
+
+
+def tc_eligible(F):
+    return (1 << min(_tc_group_bits(F.n0, F.r), max(F.h, 0))) * max(F.n0, F.r) <= 64 and F.r % 8 == 0 \
+        and F.n0 % 8 == 0
+
+
+def tc_issued_flops(F, nrhs):
+    """Tensor-core flops one apply issues: per pass, every (node, group, 128-RHS
+    tile) item runs 6 Kin/8 MMAs of 128 x 2 Nout x 8 (the same pass split as
+    the library: chunks of up to two slot bits, leaf folded into the first down
+    and the last up pass)."""
+    kmax = _tc_group_bits(F.n0, F.r)
+    chunks = [(a, min(kmax, F.h - a)) for a in range(0, F.h, kmax)] or [(0, 0)]
+    ntiles = -(-nrhs // 128)
+    total = 0
+    for half in (0, 1):
+        seq = chunks if half == 0 else chunks[::-1]
+        for i, (a, kb) in enumerate(seq):
+            G = 1 << kb
+            kin = G * (F.n0 if (half == 0 and i == 0) else F.r)
+            nout = G * (F.n0 if (half == 1 and i == len(seq) - 1) else F.r)
+            items = F.m * (F.m >> kb) * ntiles
+            total += items * 6 * (kin // 8) * 2 * 128 * (2 * nout) * 8
+    return total
 
 
 def load_traffic(kernel_name):

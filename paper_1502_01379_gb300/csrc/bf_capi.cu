@@ -633,8 +633,10 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
 }
 
 // Unit dimensions of every tensor-core pass; false if one does not fit the
-// core (Kin and Nout multiples of 16, at most 64).
+// core (Kin and Nout multiples of 16, at most 64; r and n0 multiples of 8, as
+// the epilogue stores runs of 8 outputs inside one r-block or leaf).
 bool set_tc_dims(WideDirection &D, const bf_plan_s &P) {
+    if (P.r % 8 != 0 || P.n0 % 8 != 0) return false;
     for (auto &wp : D.pass) {
         const int first = wp.st.lev[0].kind, last = wp.st.lev[wp.st.nlev - 1].kind;
         wp.Kin = wp.G * (first == bfk::LEAF_IN ? P.n0 : P.r);
@@ -950,11 +952,12 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
         cudaGetLastError();
     }
     // Multi-RHS cores for batches.  CUDA-core: built when the plan may see
-    // nrhs >= wide_min (8).  Tensor-core: built when nrhs_max >= tc_min (128)
-    // and the unit dimensions are multiples of 16 (MMA N with M = 128 RHS);
-    // each call uses the tensor-core core for batches of at least tc_min.
+    // nrhs >= wide_min (8).  Tensor-core: built when nrhs_max >= tc_min (32)
+    // and every pass's dense blocks fit the core; each call uses it for
+    // batches of at least tc_min (measured on GB300 at N = 2^20, r = 16: from
+    // 32 RHS on, 128-RHS work items beat the CUDA-core core even part-filled).
     P->wide_min = env_int("BF_WIDE_MIN", 8);
-    P->tc_min = env_int("BF_TC_MIN", 128);
+    P->tc_min = env_int("BF_TC_MIN", 32);
     if (P->nrhs_max >= P->wide_min) {
         WideCfg c;
         c.tc = false;
