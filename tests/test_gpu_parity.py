@@ -277,3 +277,27 @@ def test_full_size_n1m_r16_against_c_oracle(bf):
     a = _run(bf, plan, g, adjoint=True)
     assert _rel(a[0], capply.bf_adjoint_c(P, g[0])) < TOL
     plan.destroy()
+
+
+def test_full_size_n1m_r16_tensor_core_batch(bf):
+    """N = 2^20, L = 16, r = 16 with 128 RHS -- the batch the benchmark's
+    tensor-core line times -- on the tcgen05 core: four sampled RHS columns
+    of the apply and of the adjoint against the FP64 C loops of the oracle,
+    and, for every column, the adjoint identity <K g, f> = <g, K^* f>."""
+    from bfinputs import complex_normal, synthetic_factors
+    from oracle import capply
+    F = synthetic_factors(16, 16, 16, seed=0, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=128)
+    g = complex_normal((128, F.N), seed=5, dtype=np.complex64)
+    f = complex_normal((128, F.N), seed=6, dtype=np.complex64)
+    u = _run(bf, plan, g)
+    a = _run(bf, plan, f, adjoint=True)
+    P = capply.PreparedFactors(F)
+    for j in (0, 1, 64, 127):
+        assert _rel(u[j], capply.bf_apply_c(P, g[j])) < TOL
+        assert _rel(a[j], capply.bf_adjoint_c(P, f[j])) < TOL
+    lhs = np.einsum("ij,ij->i", u.astype(np.complex128), np.conj(f.astype(np.complex128)))
+    rhs = np.einsum("ij,ij->i", g.astype(np.complex128), np.conj(a.astype(np.complex128)))
+    scale = np.linalg.norm(u, axis=1) * np.linalg.norm(f, axis=1)
+    assert np.max(np.abs(lhs - rhs) / scale) < TOL
+    plan.destroy()
