@@ -20,6 +20,9 @@ Modules (each function cites the passage of the paper it follows):
                   in the memory-saving row-node-at-a-time order (Sec. 3.3).
 * ``apply``    -- the apply u = U^L G^{L-1}...G^h M^h (H^h)^*...(H^{L-1})^* (V^L)^* g
                   of Eq. (Kfactors) and its adjoint, one factor at a time.
+* ``grad``     -- reverse mode through the same chain: the gradient of a real
+                  loss with respect to the input and to every factor block
+                  (differentiation of the apply; PyTorch's complex convention).
 * ``sparse``   -- an independent brute-force path: every factor assembled as
                   an explicit sparse matrix from the block-matrix displays of
                   Sec. 3, and the chain multiplied out.
