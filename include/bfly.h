@@ -148,6 +148,79 @@ bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms
 bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int nrhs, long long ld,
                                   int adjoint, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiation (reverse mode).  u = K_bf g is linear in g and in each factor
+ * separately, so for a real loss with upstream gradient ubar = dL/du the
+ * gradients are gbar = K_bf^* ubar and, for every factor step y = A x of the
+ * chain, Abar = ubar-at-y x^* summed over the vectors -- for the blocks the
+ * chain uses conjugate-transposed ((V^L)^*, (H^l)^*), Bbar = x ybar^*.
+ * Complex gradients follow PyTorch's convention, dL/dRe + i dL/dIm; S^h is
+ * real and gets dL/dS.  These entry points work on factors held in device
+ * memory in the canonical layout of bf_factors (complex64, S float), so a
+ * training loop can update them in place between calls; nothing is packed.
+ * ------------------------------------------------------------------------- */
+typedef struct bf_diff_s *bf_diff;
+
+/* Device arrays of the factors (inputs), complex64 and float, canonical
+ * layout as in bf_factors; H and G are host arrays of h device pointers. */
+typedef struct {
+    const void *VL;
+    const void *const *H;
+    const float *S;
+    const void *const *G;
+    const void *UL;
+} bf_dfactors;
+
+/* Device arrays receiving the gradients, same shapes and layout as the
+ * factors; written (not accumulated) by bf_diff_backward. */
+typedef struct {
+    void *VL;
+    void *const *H;
+    float *S;
+    void *const *G;
+    void *UL;
+} bf_dgrads;
+
+typedef struct {
+    int L, leaf, r;       /* shape, as in bf_desc                                       */
+    int nrhs_max;         /* most vectors per call                                      */
+    int stride;           /* keep the input of every stride-th factor for the backward
+                             pass (1 = every factor); 0 = choose from saved_budget       */
+    size_t saved_budget;  /* with stride 0: bytes the kept inputs plus one recompute
+                             segment may take (0 = keep every factor's input)            */
+} bf_diff_desc;
+
+/* Creates a differentiation plan: validates the shape (limits of bf_desc, and
+ * 4 r^2 <= 4096, n0 r <= 4096), picks the checkpoint stride k and allocates
+ * the plan's work buffers ((2 + k - 1) vectors of max(N, 2^L r) x nrhs_max
+ * complex64).  Synchronous; *out is NULL on error. */
+bf_status bf_diff_create(bf_diff *out, const bf_diff_desc *desc);
+bf_status bf_diff_destroy(bf_diff plan);
+
+/* The checkpoint stride k the plan uses: the backward pass recomputes the
+ * inputs of the k - 1 factors after each kept one. */
+int bf_diff_stride(bf_diff plan);
+
+/* Bytes of the `saved` buffer bf_diff_forward fills for nrhs vectors (the
+ * inputs of factors 0, k, 2k, ..., position-major complex64); 0 on bad input. */
+size_t bf_diff_saved_bytes(bf_diff plan, int nrhs);
+
+/* u = K_bf g for nrhs column-major vectors (device pointers, leading
+ * dimension ld >= N, as bf_apply), keeping the checkpoints in `saved`
+ * (device, bf_diff_saved_bytes(plan, nrhs) bytes, owned by the caller and
+ * read by the matching bf_diff_backward).  Asynchronous on `stream`. */
+bf_status bf_diff_forward(bf_diff plan, const bf_dfactors *factors, const void *g, void *u, int nrhs,
+                          long long ld, void *saved, cudaStream_t stream);
+
+/* Given ubar = dL/du (device, column-major, ld as in the forward call) and
+ * the `saved` buffer of the forward call on the same factors and nrhs:
+ * gbar = K_bf^* ubar and every factor's gradient into `grads`.  Recomputes
+ * the inputs that were not kept.  The plan's work buffers are used:
+ * calls on one plan must not run concurrently on different streams.
+ * Asynchronous on `stream`. */
+bf_status bf_diff_backward(bf_diff plan, const bf_dfactors *factors, const void *ubar, void *gbar, int nrhs,
+                           long long ld, const void *saved, const bf_dgrads *grads, cudaStream_t stream);
+
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);
 

@@ -21,7 +21,8 @@ BF_C64, BF_C128 = 1, 2
 
 EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", "bf_plan_check",
            "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string",
-           "bf_apply_static_scratch")
+           "bf_apply_static_scratch", "bf_diff_create", "bf_diff_destroy", "bf_diff_stride",
+           "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward")
 
 
 class BfError(RuntimeError):
@@ -37,6 +38,19 @@ class bf_desc(ctypes.Structure):
 class bf_factors(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("VL", ctypes.c_void_p), ("H", ctypes.POINTER(ctypes.c_void_p)),
                 ("S", ctypes.c_void_p), ("G", ctypes.POINTER(ctypes.c_void_p)), ("UL", ctypes.c_void_p)]
+
+
+class bf_dfactors(ctypes.Structure):
+    _fields_ = [("VL", ctypes.c_void_p), ("H", ctypes.POINTER(ctypes.c_void_p)), ("S", ctypes.c_void_p),
+                ("G", ctypes.POINTER(ctypes.c_void_p)), ("UL", ctypes.c_void_p)]
+
+
+bf_dgrads = bf_dfactors   # same shape: device pointers (written by the backward pass)
+
+
+class bf_diff_desc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("leaf", ctypes.c_int), ("r", ctypes.c_int), ("nrhs_max", ctypes.c_int),
+                ("stride", ctypes.c_int), ("saved_budget", ctypes.c_size_t)]
 
 
 _lib = None
@@ -68,6 +82,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
         "bf_status_string": (ctypes.c_char_p, [i]),
         "bf_apply_static_scratch": (i, [vp, vp, vp, i, ll, i, vp]),
+        "bf_diff_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_diff_desc)]),
+        "bf_diff_destroy": (i, [vp]),
+        "bf_diff_stride": (i, [vp]),
+        "bf_diff_saved_bytes": (ctypes.c_size_t, [vp, i]),
+        "bf_diff_forward": (i, [vp, ctypes.POINTER(bf_dfactors), vp, vp, i, ll, vp, vp]),
+        "bf_diff_backward": (i, [vp, ctypes.POINTER(bf_dfactors), vp, vp, i, ll, vp, ctypes.POINTER(bf_dfactors),
+                                 vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -96,10 +117,16 @@ def _stream_handle(stream) -> int:
 
 
 def _addr(x) -> int:
+    """Address of a raw pointer, numpy array or torch tensor; arrays must be
+    contiguous (the ABI reads them as dense row-major buffers)."""
     if isinstance(x, int):
         return x
     if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
         return int(x.ctypes.data)
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
     return int(x.data_ptr())
 
 
@@ -203,3 +230,76 @@ def bf_apply_static_scratch(plan: Plan, x, y, nrhs: int | None = None, ld: int |
     _check(load().bf_apply_static_scratch(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi),
                                           n, l, 1 if adjoint else 0, ctypes.c_void_p(_stream_handle(stream))),
            "bf_apply_static_scratch")
+
+
+# ------------------------------------------------------------- differentiation
+class DiffPlan:
+    """Owns a bf_diff handle (reverse-mode plan)."""
+
+    def __init__(self, handle: int, L: int, n0: int, r: int, nrhs_max: int):
+        self.handle, self.L, self.n0, self.r, self.nrhs_max = handle, L, n0, r, nrhs_max
+        self.N = n0 << L
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self) -> None:
+        if getattr(self, "handle", None):
+            load().bf_diff_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def bf_diff_create(L: int, leaf: int, r: int, nrhs_max: int, stride: int = 0, saved_budget: int = 0) -> DiffPlan:
+    d = bf_diff_desc(int(L), int(leaf), int(r), int(nrhs_max), int(stride), int(saved_budget))
+    h = ctypes.c_void_p()
+    _check(load().bf_diff_create(ctypes.byref(h), ctypes.byref(d)), "bf_diff_create")
+    return DiffPlan(h.value, int(L), int(leaf), int(r), int(nrhs_max))
+
+
+def bf_diff_destroy(plan: DiffPlan) -> None:
+    plan.destroy()
+
+
+def bf_diff_stride(plan: DiffPlan) -> int:
+    return int(load().bf_diff_stride(ctypes.c_void_p(plan.handle)))
+
+
+def bf_diff_saved_bytes(plan: DiffPlan, nrhs: int) -> int:
+    return int(load().bf_diff_saved_bytes(ctypes.c_void_p(plan.handle), int(nrhs)))
+
+
+def _dfactors(VL, H, S, G, UL):
+    """bf_dfactors of device tensors (or addresses); returns (struct, keep-alive)."""
+    nh = max(1, len(H))
+    h_arr = (ctypes.c_void_p * nh)(*[_addr(a) for a in H])
+    g_arr = (ctypes.c_void_p * nh)(*[_addr(a) for a in G])
+    f = bf_dfactors(_addr(VL), ctypes.cast(h_arr, ctypes.POINTER(ctypes.c_void_p)), _addr(S),
+                    ctypes.cast(g_arr, ctypes.POINTER(ctypes.c_void_p)), _addr(UL))
+    return f, (h_arr, g_arr)
+
+
+def bf_diff_forward(plan: DiffPlan, factors, g, u, saved, nrhs: int | None = None, ld: int | None = None,
+                    stream=None) -> None:
+    """u = K_bf g keeping checkpoints in `saved`; factors = (VL, H, S, G, UL) device tensors."""
+    f, keep = _dfactors(*factors)
+    n = (1 if g.ndim == 1 else int(g.shape[0])) if nrhs is None else int(nrhs)
+    _check(load().bf_diff_forward(ctypes.c_void_p(plan.handle), ctypes.byref(f), ctypes.c_void_p(_addr(g)),
+                                  ctypes.c_void_p(_addr(u)), n, int(ld or plan.N), ctypes.c_void_p(_addr(saved)),
+                                  ctypes.c_void_p(_stream_handle(stream))), "bf_diff_forward")
+    del keep
+
+
+def bf_diff_backward(plan: DiffPlan, factors, ubar, gbar, saved, grads, nrhs: int | None = None,
+                     ld: int | None = None, stream=None) -> None:
+    """gbar = K_bf^* ubar and the factor gradients into grads = (VL, H, S, G, UL)."""
+    f, keep = _dfactors(*factors)
+    gr, keep2 = _dfactors(*grads)
+    n = (1 if ubar.ndim == 1 else int(ubar.shape[0])) if nrhs is None else int(nrhs)
+    _check(load().bf_diff_backward(ctypes.c_void_p(plan.handle), ctypes.byref(f), ctypes.c_void_p(_addr(ubar)),
+                                   ctypes.c_void_p(_addr(gbar)), n, int(ld or plan.N),
+                                   ctypes.c_void_p(_addr(saved)), ctypes.byref(gr),
+                                   ctypes.c_void_p(_stream_handle(stream))), "bf_diff_backward")
+    del keep, keep2

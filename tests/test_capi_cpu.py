@@ -20,7 +20,7 @@ def lib():
 
 def _declared(repo_root):
     text = open(os.path.join(repo_root, "include", "bfly.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:bf_status|size_t|const char \*)\s*(bf_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:bf_status|size_t|int|const char \*)\s*(bf_\w+)\s*\(", text, re.M)))
 
 
 def test_header_declares_the_abi(repo_root):
