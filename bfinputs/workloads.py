@@ -106,3 +106,37 @@ def sample_rows(N: int, count: int = 256, seed: int = 0) -> np.ndarray:
     """A sorted random set of ``count`` distinct rows (the set S of the
     accuracy measure epsilon^a in Sec. 4 has 256 points)."""
     return np.sort(_rng(seed, 31337).choice(N, size=min(count, N), replace=False))
+
+
+@dataclass(frozen=True)
+class BatchMember:
+    """One operator of the batched workload: its tree shape, rank, vector
+    count and the FIO parameters c(x) = (2 + a sin(2 pi x + phi)) / 8 it stands for."""
+    L: int
+    n0: int
+    r: int
+    nrhs: int
+    a: float
+    phi: float
+
+    @property
+    def N(self) -> int:
+        return self.n0 << self.L
+
+
+def batched_workload(count: int = 256, seed: int = 3, min_log2n: int = 10, max_log2n: int = 16,
+                     ranks=(8, 12, 16), max_nrhs: int = 32) -> list:
+    """The batched workload's operators: N log-uniform over 2^min_log2n ..
+    2^max_log2n (the exponent uniform), r uniform over `ranks`, nrhs uniform
+    over 1..max_nrhs, a ~ U[0.5, 1], phi ~ U[0, 2 pi).  Trees have even depth:
+    leaf 16 when log2 N - 4 is even, else leaf 32 (L = log2 N - 5)."""
+    rng = _rng(seed, 0xBA7C)
+    out = []
+    for _ in range(count):
+        e = int(rng.integers(min_log2n, max_log2n + 1))
+        n0 = 16 if (e - 4) % 2 == 0 else 32
+        L = e - (4 if n0 == 16 else 5)
+        r = int(ranks[int(rng.integers(0, len(ranks)))])
+        nrhs = int(rng.integers(1, max_nrhs + 1))
+        out.append(BatchMember(L, n0, r, nrhs, float(rng.uniform(0.5, 1.0)), float(rng.uniform(0, 2 * np.pi))))
+    return out

@@ -149,6 +149,53 @@ bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int n
                                   int adjoint, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Batches of independent factorizations.  Many operators -- each its own
+ * shape (L, n0, r) and its own number of vectors -- applied together: every
+ * operator's down half runs in one grouped launch (one thread block per
+ * operator, middle-level node and RHS tile, largest operators first), then
+ * every up half in a second, optionally replayed from a CUDA graph.  Each
+ * operator is the fused path of bf_apply with its own factors, packed with
+ * the batch's ring configuration.
+ * ------------------------------------------------------------------------- */
+typedef struct bf_batch_s *bf_batch;
+
+typedef struct {
+    int T;          /* RHS per thread block: 1, 2 or 4 (0 = 1)                      */
+    int slot_kb;    /* factor ring slot size in KB (0 = 16)                          */
+    int stages;     /* ring slots (0 = 2)                                            */
+} bf_batch_config;
+
+typedef enum {
+    BF_BATCH_EACH = 0,     /* one operator at a time (two launches per operator)          */
+    BF_BATCH_GROUPED = 1,  /* two grouped launches for the whole batch                    */
+    BF_BATCH_GRAPH = 2,    /* the grouped launches captured once in a CUDA graph, replayed */
+} bf_batch_mode;
+
+/* Builds a batch of n operators: descs[o] and factors[o] as in bf_plan_create
+ * (descs[o].nrhs_max >= nrhs[o]); the vectors are bound here: in[o], out[o]
+ * are DEVICE pointers to column-major N_o x nrhs[o] complex64 arrays with
+ * leading dimension ld[o] (in[o] and out[o] must not overlap).  cfg may be
+ * NULL.  Synchronous.  Limits as bf_plan_create; BF_ERR_UNSUPPORTED if an
+ * operator's thread block does not fit the ring configuration. */
+bf_status bf_batch_create(bf_batch *batch, int n, const bf_desc *descs, const bf_factors *factors,
+                          const void *const *in, void *const *out, const int *nrhs, const long long *ld,
+                          const bf_batch_config *cfg, cudaStream_t stream);
+
+/* out[o] = K_o in[o] (adjoint = 0) or K_o^* in[o] for every operator of the
+ * batch, by the given bf_batch_mode, asynchronously on `stream`.  The first
+ * BF_BATCH_GRAPH call per direction captures and instantiates the graph
+ * (on a private stream; call it before capturing anything else yourself). */
+bf_status bf_batch_apply(bf_batch batch, int adjoint, int mode, cudaStream_t stream);
+
+/* As bf_plan_check, over every operator of the batch. */
+bf_status bf_batch_check(bf_batch batch, cudaStream_t stream);
+
+/* Thread blocks per grouped launch. */
+int bf_batch_items(bf_batch batch);
+
+bf_status bf_batch_destroy(bf_batch batch);
+
+/* ---------------------------------------------------------------------------
  * Differentiation (reverse mode).  u = K_bf g is linear in g and in each factor
  * separately, so for a real loss with upstream gradient ubar = dL/du the
  * gradients are gbar = K_bf^* ubar and, for every factor step y = A x of the

@@ -22,7 +22,9 @@ BF_C64, BF_C128 = 1, 2
 EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", "bf_plan_check",
            "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string",
            "bf_apply_static_scratch", "bf_diff_create", "bf_diff_destroy", "bf_diff_stride",
-           "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward")
+           "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
+           "bf_batch_check", "bf_batch_items", "bf_batch_destroy")
+BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
 
 class BfError(RuntimeError):
@@ -46,6 +48,10 @@ class bf_dfactors(ctypes.Structure):
 
 
 bf_dgrads = bf_dfactors   # same shape: device pointers (written by the backward pass)
+
+
+class bf_batch_config(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("slot_kb", ctypes.c_int), ("stages", ctypes.c_int)]
 
 
 class bf_diff_desc(ctypes.Structure):
@@ -82,6 +88,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
         "bf_status_string": (ctypes.c_char_p, [i]),
         "bf_apply_static_scratch": (i, [vp, vp, vp, i, ll, i, vp]),
+        "bf_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(bf_desc), ctypes.POINTER(bf_factors),
+                                ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
+                                ctypes.POINTER(ll), ctypes.POINTER(bf_batch_config), vp]),
+        "bf_batch_apply": (i, [vp, i, i, vp]),
+        "bf_batch_check": (i, [vp, vp]),
+        "bf_batch_items": (i, [vp]),
+        "bf_batch_destroy": (i, [vp]),
         "bf_diff_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_diff_desc)]),
         "bf_diff_destroy": (i, [vp]),
         "bf_diff_stride": (i, [vp]),
@@ -148,9 +161,8 @@ class Plan:
             self.handle = None
 
 
-def bf_plan_create(factors, nrhs_max: int = 1, stream=None) -> Plan:
-    """Create a plan from factors in canonical layout (any object with L, n0,
-    r, VL, H, S, G, UL as numpy arrays; complex64 or complex128)."""
+def _host_factors(factors):
+    """bf_factors of host arrays (complex64 or complex128); returns (struct, keep-alive)."""
     c128 = np.asarray(factors.VL).dtype == np.complex128
     cdt, rdt = (np.complex128, np.float64) if c128 else (np.complex64, np.float32)
     keep = [np.ascontiguousarray(factors.VL, cdt), np.ascontiguousarray(factors.UL, cdt),
@@ -163,11 +175,18 @@ def bf_plan_create(factors, nrhs_max: int = 1, stream=None) -> Plan:
     f = bf_factors(BF_C128 if c128 else BF_C64, keep[0].ctypes.data,
                    ctypes.cast(h_arr, ctypes.POINTER(ctypes.c_void_p)), keep[2].ctypes.data,
                    ctypes.cast(g_arr, ctypes.POINTER(ctypes.c_void_p)), keep[1].ctypes.data)
+    return f, (keep, Hs, Gs, h_arr, g_arr)
+
+
+def bf_plan_create(factors, nrhs_max: int = 1, stream=None) -> Plan:
+    """Create a plan from factors in canonical layout (any object with L, n0,
+    r, VL, H, S, G, UL as numpy arrays; complex64 or complex128)."""
+    f, keep = _host_factors(factors)
     d = bf_desc(int(factors.L), int(factors.n0), int(factors.r), int(nrhs_max))
     h = ctypes.c_void_p()
     _check(load().bf_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.byref(f),
                                  ctypes.c_void_p(_stream_handle(stream))), "bf_plan_create")
-    del keep, Hs, Gs
+    del keep
     return Plan(h.value, int(factors.n0) << int(factors.L), int(factors.L), int(factors.n0),
                 int(factors.r), int(nrhs_max))
 
@@ -303,3 +322,65 @@ def bf_diff_backward(plan: DiffPlan, factors, ubar, gbar, saved, grads, nrhs: in
                                    ctypes.c_void_p(_addr(saved)), ctypes.byref(gr),
                                    ctypes.c_void_p(_stream_handle(stream))), "bf_diff_backward")
     del keep, keep2
+
+
+# ----------------------------------------------------------------- batches
+class Batch:
+    """Owns a bf_batch handle; keeps the bound vectors alive."""
+
+    def __init__(self, handle: int, n: int, keep):
+        self.handle, self.n, self._keep = handle, n, keep
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self) -> None:
+        if getattr(self, "handle", None):
+            load().bf_batch_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def bf_batch_create(factors_list, ins, outs, nrhs, T: int = 1, slot_kb: int = 0, stages: int = 0,
+                    stream=None) -> Batch:
+    """A batch of operators (factors in canonical layout, host arrays) bound to
+    device vectors ins[o], outs[o] of shape (nrhs[o], N_o) complex64."""
+    n = len(factors_list)
+    descs = (bf_desc * n)()
+    facs = (bf_factors * n)()
+    keep = []
+    for o, F in enumerate(factors_list):
+        descs[o] = bf_desc(int(F.L), int(F.n0), int(F.r), int(nrhs[o]))
+        f, k = _host_factors(F)
+        facs[o] = f
+        keep.append(k)
+    in_arr = (ctypes.c_void_p * n)(*[_addr(x) for x in ins])
+    out_arr = (ctypes.c_void_p * n)(*[_addr(x) for x in outs])
+    nr = (ctypes.c_int * n)(*[int(x) for x in nrhs])
+    lds = (ctypes.c_longlong * n)(*[int(F.n0) << int(F.L) for F in factors_list])
+    cfg = bf_batch_config(int(T), int(slot_kb), int(stages))
+    h = ctypes.c_void_p()
+    _check(load().bf_batch_create(ctypes.byref(h), n, descs, facs, in_arr, out_arr, nr, lds, ctypes.byref(cfg),
+                                  ctypes.c_void_p(_stream_handle(stream))), "bf_batch_create")
+    del keep
+    return Batch(h.value, n, (list(ins), list(outs)))
+
+
+def bf_batch_apply(batch: Batch, adjoint: bool = False, mode: int = BF_BATCH_GRAPH, stream=None) -> None:
+    _check(load().bf_batch_apply(ctypes.c_void_p(batch.handle), 1 if adjoint else 0, int(mode),
+                                 ctypes.c_void_p(_stream_handle(stream))), "bf_batch_apply")
+
+
+def bf_batch_check(batch: Batch, stream=None) -> None:
+    _check(load().bf_batch_check(ctypes.c_void_p(batch.handle), ctypes.c_void_p(_stream_handle(stream))),
+           "bf_batch_check")
+
+
+def bf_batch_items(batch: Batch) -> int:
+    return int(load().bf_batch_items(ctypes.c_void_p(batch.handle)))
+
+
+def bf_batch_destroy(batch: Batch) -> None:
+    batch.destroy()

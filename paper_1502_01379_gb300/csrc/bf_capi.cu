@@ -534,9 +534,13 @@ int wide_nr_max(const bf_plan_s &P, const WideCfg &c) {
     return 0;
 }
 
+// The dynamic shared memory attribute of a kernel is one value shared by every
+// plan that launches it, so it is always set to the device's opt-in maximum
+// (an upper bound; each launch still requests only what it uses).
 template <int NR>
 bf_status set_wide_attr(size_t bytes) {
-    BF_CUDA(cudaFuncSetAttribute(bfw::bf_wide_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    (void)bytes;
+    BF_CUDA(cudaFuncSetAttribute(bfw::bf_wide_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     return BF_OK;
 }
 
@@ -652,8 +656,9 @@ size_t plan_smem(const bf_plan_s &P, int T) { return bfk::smem_bytes(P.stages, P
 
 template <int T>
 bf_status set_smem_attr(size_t bytes) {
-    BF_CUDA(cudaFuncSetAttribute(bfk::bf_down_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    BF_CUDA(cudaFuncSetAttribute(bfk::bf_up_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    (void)bytes;   // shared by all plans: the opt-in maximum (see set_wide_attr)
+    BF_CUDA(cudaFuncSetAttribute(bfk::bf_down_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    BF_CUDA(cudaFuncSetAttribute(bfk::bf_up_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     return BF_OK;
 }
 
@@ -886,7 +891,29 @@ cudaError_t launch_pair_static(const bf_plan_s &P, const Direction &D, const flo
 
 extern "C" {
 
-bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f, cudaStream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// Ring and path configuration of a plan.
+struct PlanCfg {
+    int consumers = 256;
+    int slot_kb = 64;
+    int stages = 3;
+    size_t smem_limit = kMaxSmem;
+    bool fused_only = false;   // no multi-RHS cores (grouped batches use the fused kernels)
+};
+
+PlanCfg env_plan_cfg() {
+    PlanCfg c;
+    c.consumers = std::min(256, std::max(32, env_int("BF_CONSUMERS", 256) / 32 * 32));
+    c.slot_kb = env_int("BF_SLOT_KB", 64);
+    c.stages = std::max(2, env_int("BF_STAGES", 3));
+    return c;
+}
+
+bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, cudaStream_t stream,
+                      const PlanCfg &cfg) {
     if (!plan) return BF_ERR_INVALID;
     *plan = nullptr;
     if (!desc || !f) return BF_ERR_INVALID;
@@ -917,13 +944,13 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
     // whole 2r x 2r butterfly (4r^2) and a whole leaf (n0 r).
     // Defaults measured on GB300 at N = 2^20, r = 16: 256 consumers, 64 KB
     // slots and as many slots as fit (2 there) stream at the HBM copy rate.
-    P->consumers = std::min(256, std::max(32, env_int("BF_CONSUMERS", 256) / 32 * 32));
-    int slot_len = env_int("BF_SLOT_KB", 64) * 128;
+    P->consumers = cfg.consumers;
+    int slot_len = cfg.slot_kb * 128;
     slot_len = std::max(slot_len, std::max(4 * r * r, n0 * r + 1));
     P->slot_len = (slot_len + 1) & ~1;
-    P->stages = std::max(2, env_int("BF_STAGES", 3));
-    while (P->stages > 2 && plan_smem(*P, 1) > (size_t)kMaxSmem) --P->stages;
-    if (plan_smem(*P, 1) > (size_t)kMaxSmem) {
+    P->stages = std::max(2, cfg.stages);
+    while (P->stages > 2 && plan_smem(*P, 1) > cfg.smem_limit) --P->stages;
+    if (plan_smem(*P, 1) > cfg.smem_limit) {
         delete P;
         return BF_ERR_UNSUPPORTED;
     }
@@ -956,8 +983,8 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
     // and every pass's dense blocks fit the core; each call uses it for
     // batches of at least tc_min (measured on GB300 at N = 2^20, r = 16: from
     // 32 RHS on, 128-RHS work items beat the CUDA-core core even part-filled).
-    P->wide_min = env_int("BF_WIDE_MIN", 8);
-    P->tc_min = env_int("BF_TC_MIN", 32);
+    P->wide_min = cfg.fused_only ? (1 << 30) : env_int("BF_WIDE_MIN", 8);
+    P->tc_min = cfg.fused_only ? (1 << 30) : env_int("BF_TC_MIN", 32);
     if (P->nrhs_max >= P->wide_min) {
         WideCfg c;
         c.tc = false;
@@ -1020,6 +1047,14 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
         return fail(cuda_fail(cudaErrorUnknown));
     *plan = P;
     return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f, cudaStream_t stream) {
+    return create_plan(plan, desc, f, stream, env_plan_cfg());
 }
 
 bf_status bf_apply(bf_plan plan, const void *in, void *out, int nrhs, long long ld, cudaStream_t stream) {
@@ -1115,6 +1150,212 @@ const char *bf_status_string(bf_status s) {
         case BF_ERR_TIMEOUT: return "BF_ERR_TIMEOUT: a kernel wait expired";
     }
     return "unknown bf_status";
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent operators (bf_batch_*): one internal fused-path plan
+// per operator, all of them run by two grouped launches (every operator's
+// down half, then every up half), optionally replayed from a CUDA graph.
+
+struct bf_batch_s {
+    int n = 0, T = 1, nitems = 0;
+    std::vector<bf_plan> plans;
+    Params *d_params = nullptr;           // [fwd down, fwd up, adj down, adj up] x n
+    bfk::GroupItem *d_items = nullptr;    // (operator, node, RHS tile), largest operators first
+    size_t smem = 0;                      // dynamic shared memory of the grouped launches
+    std::vector<const void *> in;
+    std::vector<void *> out;
+    std::vector<int> nrhs;
+    std::vector<long long> ld;
+    cudaStream_t cap = nullptr;           // private stream for graph capture
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+template <int T>
+cudaError_t launch_grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
+    const Params *pl = B.d_params + (adjoint ? 2 : 0) * B.n;
+    bfk::bf_down_grouped<T><<<B.nitems, 256 + 32, B.smem, s>>>(pl, B.d_items);
+    bfk::bf_up_grouped<T><<<B.nitems, 256 + 32, B.smem, s>>>(pl + B.n, B.d_items);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
+    return B.T == 4 ? launch_grouped<4>(B, adjoint, s) : B.T == 2 ? launch_grouped<2>(B, adjoint, s)
+                                                                  : launch_grouped<1>(B, adjoint, s);
+}
+
+template <int T>
+bf_status set_grouped_attr(size_t bytes) {
+    (void)bytes;   // shared by all batches: the maximum next to the static Params copy
+    BF_CUDA(cudaFuncSetAttribute(bfk::bf_down_grouped<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMaxSmem - 1024));
+    BF_CUDA(cudaFuncSetAttribute(bfk::bf_up_grouped<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kMaxSmem - 1024));
+    return BF_OK;
+}
+
+void free_batch(bf_batch_s *B) {
+    if (!B) return;
+    for (auto &e : B->exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    cudaFree(B->d_params);
+    cudaFree(B->d_items);
+    for (bf_plan p : B->plans) free_plan(p);
+    cudaGetLastError();
+    delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_factors *factors,
+                          const void *const *in, void *const *outv, const int *nrhs, const long long *ld,
+                          const bf_batch_config *cfg, cudaStream_t stream) {
+    if (!out) return BF_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || !descs || !factors || !in || !outv || !nrhs || !ld) return BF_ERR_INVALID;
+    const int T = cfg && cfg->T ? cfg->T : 1;
+    if (T != 1 && T != 2 && T != 4) return BF_ERR_INVALID;
+    for (int o = 0; o < n; ++o) {
+        if (!in[o] || !outv[o] || nrhs[o] < 1 || nrhs[o] > descs[o].nrhs_max) return BF_ERR_INVALID;
+        if (ld[o] < ((long long)descs[o].leaf << descs[o].L)) return BF_ERR_INVALID;
+        if (is_host_pointer(in[o]) || is_host_pointer(outv[o])) return BF_ERR_INVALID;
+    }
+    bf_batch_s *B = new (std::nothrow) bf_batch_s();
+    if (!B) return BF_ERR_NOMEM;
+    B->n = n;
+    B->T = T;
+    PlanCfg pc;
+    pc.consumers = 256;
+    pc.slot_kb = cfg && cfg->slot_kb ? cfg->slot_kb : 16;
+    pc.stages = cfg && cfg->stages ? cfg->stages : 2;
+    pc.fused_only = true;
+    pc.smem_limit = kMaxSmem - 2048;   // the grouped kernels' Params copy is static shared memory
+    std::vector<Params> host(4 * (size_t)n);
+    std::vector<bfk::GroupItem> items;
+    std::vector<std::pair<long long, int>> order;   // (work, operator)
+    for (int o = 0; o < n; ++o) {
+        bf_plan P = nullptr;
+        bf_status st = create_plan(&P, &descs[o], &factors[o], stream, pc);
+        if (st != BF_OK) {
+            free_batch(B);
+            return st;
+        }
+        B->plans.push_back(P);
+        if (plan_smem(*P, T) > pc.smem_limit) {
+            free_batch(B);
+            return BF_ERR_UNSUPPORTED;
+        }
+        B->smem = std::max(B->smem, plan_smem(*P, T));
+        for (int dir = 0; dir < 2; ++dir) {
+            const Direction &D = dir ? P->adj : P->fwd;
+            Params pd = base_params(*P, D.down);
+            pd.in = static_cast<const float2 *>(in[o]);
+            pd.ld_in = ld[o];
+            pd.out = P->d_ws;
+            pd.ld_out = P->R;
+            pd.nrhs = nrhs[o];
+            Params pu = base_params(*P, D.up);
+            pu.in = P->d_ws;
+            pu.ld_in = P->R;
+            pu.out = static_cast<float2 *>(outv[o]);
+            pu.ld_out = ld[o];
+            pu.S = D.d_S;
+            pu.nrhs = nrhs[o];
+            host[(size_t)(2 * dir) * n + o] = pd;
+            host[(size_t)(2 * dir + 1) * n + o] = pu;
+        }
+        order.push_back({(long long)P->m * ((nrhs[o] + T - 1) / T) * (P->fwd.down.cta_len + P->fwd.up.cta_len), o});
+        B->in.push_back(in[o]);
+        B->out.push_back(outv[o]);
+        B->nrhs.push_back(nrhs[o]);
+        B->ld.push_back(ld[o]);
+    }
+    std::sort(order.begin(), order.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    for (auto &w : order) {
+        const bf_plan_s &P = *B->plans[w.second];
+        for (int node = 0; node < P.m; ++node)
+            for (int r0 = 0; r0 < nrhs[w.second]; r0 += T) items.push_back({w.second, node, r0, 0});
+    }
+    B->nitems = (int)items.size();
+    bf_status st = BF_OK;
+    st = T == 4 ? set_grouped_attr<4>(B->smem) : T == 2 ? set_grouped_attr<2>(B->smem) : set_grouped_attr<1>(B->smem);
+    if (st != BF_OK) {
+        free_batch(B);
+        return st;
+    }
+    if (cudaMalloc(&B->d_params, host.size() * sizeof(Params)) != cudaSuccess ||
+        cudaMalloc(&B->d_items, items.size() * sizeof(bfk::GroupItem)) != cudaSuccess ||
+        cudaMemcpy(B->d_params, host.data(), host.size() * sizeof(Params), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(bfk::GroupItem), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        free_batch(B);
+        return cuda_fail(cudaErrorMemoryAllocation);
+    }
+    *out = B;
+    return BF_OK;
+}
+
+bf_status bf_batch_apply(bf_batch B, int adjoint, int mode, cudaStream_t stream) {
+    if (!B || mode < 0 || mode > 2) return BF_ERR_INVALID;
+    const bool adj = adjoint != 0;
+    if (mode == BF_BATCH_EACH) {   // one plan at a time: two launches per operator
+        for (int o = 0; o < B->n; ++o) {
+            bf_status st = run(B->plans[o], B->in[o], B->out[o], B->nrhs[o], B->ld[o], stream, adj);
+            if (st != BF_OK) return st;
+        }
+        return BF_OK;
+    }
+    if (mode == BF_BATCH_GROUPED) {
+        cudaError_t e = grouped(*B, adj, stream);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e);
+    }
+    // BF_BATCH_GRAPH: the two grouped launches captured once into a graph, then replayed.
+    cudaGraphExec_t &ex = B->exec[adj ? 1 : 0];
+    if (!ex) {
+        if (!B->cap) BF_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        BF_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t e = grouped(*B, adj, B->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e != cudaSuccess ? e : e2);
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) {
+            ex = nullptr;
+            return cuda_fail(e3);
+        }
+    }
+    BF_CUDA(cudaGraphLaunch(ex, stream));
+    return BF_OK;
+}
+
+bf_status bf_batch_check(bf_batch B, cudaStream_t stream) {
+    if (!B) return BF_ERR_INVALID;
+    bf_status worst = BF_OK;
+    for (bf_plan p : B->plans) {
+        const bf_status st = bf_plan_check(p, stream);
+        if (st != BF_OK) worst = st;
+    }
+    return worst;
+}
+
+int bf_batch_items(bf_batch B) { return B ? B->nitems : 0; }
+
+bf_status bf_batch_destroy(bf_batch B) {
+    if (!B) return BF_OK;
+    cudaDeviceSynchronize();
+    free_batch(B);
+    return BF_OK;
 }
 
 }  // extern "C"

@@ -419,8 +419,10 @@ bf_status bf_diff_create(bf_diff *out, const bf_diff_desc *d) {
     P->k = std::min(std::max(k, 1), P->nf);
     P->work_vec = (size_t)vec;
     const size_t nvec = 2 + (size_t)(P->k - 1);
-    const int sm = (int)std::max(bfd::unit_smem(2, d->r, q), bfd::unit_smem(1, d->leaf, d->r));
-    if (cudaFuncSetAttribute(bfd::unit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) {
+    // One attribute value shared by every plan: the opt-in maximum (an upper
+    // bound; each launch requests only its unit's shared memory).
+    if (cudaFuncSetAttribute(bfd::unit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess) {
         cudaGetLastError();
         delete P;
         return BF_ERR_CUDA;

@@ -339,10 +339,9 @@ __device__ __forceinline__ void store_row(const Params &p, const Level &lv, floa
 // adjacent rows of one unit when the unit's row count is even.
 template <int T, int KIND>
 __device__ __forceinline__ void run_level(const Params &p, const Smem &s, const Level &lv, float2 *xin,
-                                          float2 *xout, uint32_t &gs, int nconsumers, int rhs0, int nt) {
+                                          float2 *xout, uint32_t &gs, int nconsumers, int node, int rhs0, int nt) {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int node = blockIdx.y;
     const int rows = lv.upb * lv.rpu;
     const bool pair = (lv.rpu & 1) == 0;
     const int nitems = pair ? rows >> 1 : rows;
@@ -392,16 +391,17 @@ __device__ __forceinline__ void run_level(const Params &p, const Smem &s, const 
 // Runs the levels [0, nlev) of this CTA on the segment buffers; returns the
 // buffer that holds the last level's output.
 template <int T>
-__device__ __forceinline__ float2 *run_levels(const Params &p, const Smem &s, int nconsumers, int rhs0, int nt) {
+__device__ __forceinline__ float2 *run_levels(const Params &p, const Smem &s, int nconsumers, int node, int rhs0,
+                                              int nt) {
     float2 *xin = s.buf0, *xout = s.buf1;
     uint32_t gs = 0;
     for (int l = 0; l < p.nlev; ++l) {
         const Level lv = p.lev[l];
         switch (lv.kind) {
-            case LEAF_IN: run_level<T, LEAF_IN>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
-            case MERGE: run_level<T, MERGE>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
-            case SPLIT: run_level<T, SPLIT>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
-            default: run_level<T, LEAF_OUT>(p, s, lv, xin, xout, gs, nconsumers, rhs0, nt); break;
+            case LEAF_IN: run_level<T, LEAF_IN>(p, s, lv, xin, xout, gs, nconsumers, node, rhs0, nt); break;
+            case MERGE: run_level<T, MERGE>(p, s, lv, xin, xout, gs, nconsumers, node, rhs0, nt); break;
+            case SPLIT: run_level<T, SPLIT>(p, s, lv, xin, xout, gs, nconsumers, node, rhs0, nt); break;
+            default: run_level<T, LEAF_OUT>(p, s, lv, xin, xout, gs, nconsumers, node, rhs0, nt); break;
         }
         consumer_sync(nconsumers);
         float2 *tmp = xin;
@@ -412,18 +412,18 @@ __device__ __forceinline__ float2 *run_levels(const Params &p, const Smem &s, in
 }
 
 // ------------------------------------------------------------------ kernels
+// Down half of one CTA: column node `node` (tree node at level h), RHS tile
+// starting at rhs0 (tiles of one node are adjacent in the grid, so they share
+// its factors in L2).
 template <int T>
-__global__ void __launch_bounds__(288, 1) bf_down_kernel(const Params p) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void down_body(const Params &p, unsigned char *smem_raw, int node, int rhs0) {
     const int nconsumers = blockDim.x - 32;
     const Smem s = carve<T>(p, smem_raw);
     setup<T>(p, s, nconsumers);
     const int tid = threadIdx.x;
-    const int node = blockIdx.y;          // tree node at level h
-    const int rhs0 = blockIdx.x * T;      // RHS tile (fastest: tiles of one node share its factors in L2)
     const int nt = min(T, p.nrhs - rhs0);
     if (tid >= nconsumers) {
-        if (tid == nconsumers) produce(p, blockIdx.y, s.ring, s.full, s.empty, s.abort_flag);
+        if (tid == nconsumers) produce(p, node, s.ring, s.full, s.empty, s.abort_flag);
     } else {
         // Input points of column node `node`: n0*m consecutive entries per RHS.
         const int nin = p.n0 * p.m;
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(288, 1) bf_down_kernel(const Params p) {
             s.buf0[e] = (t < nt) ? __ldg(p.in + (long long)(rhs0 + t) * p.ld_in + base + ee) : make_float2(0.f, 0.f);
         }
         consumer_sync(nconsumers);
-        const float2 *res = run_levels<T>(p, s, nconsumers, rhs0, nt);
+        const float2 *res = run_levels<T>(p, s, nconsumers, node, rhs0, nt);
         // Segment `node` of the level-h vector: m*r consecutive entries per RHS.
         const int nseg = p.m * p.r;
         const long long obase = (long long)node * nseg;
@@ -445,18 +445,16 @@ __global__ void __launch_bounds__(288, 1) bf_down_kernel(const Params p) {
     __syncthreads();
 }
 
+// Up half of one CTA: row node `node`, RHS tile starting at rhs0.
 template <int T>
-__global__ void __launch_bounds__(288, 1) bf_up_kernel(const Params p) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void up_body(const Params &p, unsigned char *smem_raw, int node, int rhs0) {
     const int nconsumers = blockDim.x - 32;
     const Smem s = carve<T>(p, smem_raw);
     setup<T>(p, s, nconsumers);
     const int tid = threadIdx.x;
-    const int node = blockIdx.y;          // tree node at level h
-    const int rhs0 = blockIdx.x * T;      // RHS tile (fastest: tiles of one node share its factors in L2)
     const int nt = min(T, p.nrhs - rhs0);
     if (tid >= nconsumers) {
-        if (tid == nconsumers) produce(p, blockIdx.y, s.ring, s.full, s.empty, s.abort_flag);
+        if (tid == nconsumers) produce(p, node, s.ring, s.full, s.empty, s.abort_flag);
     } else {
         // M^h: local block q <- S[node, q] * (block q*m + node of the level-h vector).
         const int nseg = p.m * p.r;
@@ -472,9 +470,49 @@ __global__ void __launch_bounds__(288, 1) bf_up_kernel(const Params p) {
             s.buf0[e] = v;
         }
         consumer_sync(nconsumers);
-        run_levels<T>(p, s, nconsumers, rhs0, nt);
+        run_levels<T>(p, s, nconsumers, node, rhs0, nt);
     }
     __syncthreads();
+}
+
+template <int T>
+__global__ void __launch_bounds__(288, 1) bf_down_kernel(const Params p) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    down_body<T>(p, smem_raw, blockIdx.y, blockIdx.x * T);
+}
+
+template <int T>
+__global__ void __launch_bounds__(288, 1) bf_up_kernel(const Params p) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    up_body<T>(p, smem_raw, blockIdx.y, blockIdx.x * T);
+}
+
+// Grouped launches: many operators (each its own Params) in one grid.  CTA i
+// runs work item items[i] = (operator, node, RHS tile) with that operator's
+// Params, copied to shared memory first.  Register-bounded for two CTAs per
+// SM: batches are mostly small operators whose CTAs need little shared memory.
+struct GroupItem {
+    int op, node, rhs0, pad_;
+};
+
+template <int T>
+__global__ void __launch_bounds__(288, 2) bf_down_grouped(const Params *plist, const GroupItem *items) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Params sp;
+    const GroupItem it = items[blockIdx.x];
+    if (threadIdx.x == 0) sp = plist[it.op];
+    __syncthreads();
+    down_body<T>(sp, smem_raw, it.node, it.rhs0);
+}
+
+template <int T>
+__global__ void __launch_bounds__(288, 2) bf_up_grouped(const Params *plist, const GroupItem *items) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Params sp;
+    const GroupItem it = items[blockIdx.x];
+    if (threadIdx.x == 0) sp = plist[it.op];
+    __syncthreads();
+    up_body<T>(sp, smem_raw, it.node, it.rhs0);
 }
 
 }  // namespace bfk
