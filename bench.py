@@ -47,6 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation line")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-operators line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -303,7 +304,47 @@ def run_ours(args, rank, world, local):
     del F, g, u, v, gh, uh, vh
     if not args.no_diff:
         out["differentiation"] = diff_line(dev, stream)
+    if not args.no_batch:
+        out["batched"] = batch_line(dev, stream)
     return out
+
+
+def batch_line(dev, stream):
+    """The batched workload: 256 independent operators (N log-uniform over
+    2^10..2^16, r in {8, 12, 16}, 1..32 RHS each, seeded synthetic factor
+    values), applied then adjoint-applied as one batch: one operator at a
+    time (two launches each) versus two grouped launches replayed from a CUDA
+    graph, with the autotuned RHS tile and factor ring."""
+    import numpy as np
+    import torch
+
+    from paper_1502_01379_gb300 import batch as B
+    from paper_1502_01379_gb300 import capi
+    from bfinputs import batched_workload, complex_normal, synthetic_factors
+    members = batched_workload()
+    Fs = [synthetic_factors(m.L, m.n0, m.r, seed=2000 + i, dtype=np.complex64) for i, m in enumerate(members)]
+    ins = [torch.from_numpy(complex_normal((m.nrhs, m.N), seed=3000 + i, dtype=np.complex64)).to(dev)
+           for i, m in enumerate(members)]
+    outs = [torch.empty_like(x) for x in ins]
+    nrhs = [m.nrhs for m in members]
+    cand = [(T, kb, st) for T in (1, 2, 4) for (kb, st) in ((16, 2), (64, 2))]
+    cfg = B.autotune(Fs, ins, outs, nrhs, candidates=cand, reps=3)
+    b = capi.bf_batch_create(Fs, ins, outs, nrhs, T=cfg["T"], slot_kb=cfg["slot_kb"], stages=cfg["stages"])
+    vecs = 2 * sum(nrhs)                 # apply + adjoint of every operator's vectors
+    res = {"workload": "batched: 256 independent butterfly factorizations of 1D-FIO-shaped matrices, N "
+                       "log-uniform over 2^10..2^16 (leaf 16 or 32), r in {8,12,16}, 1..32 RHS each, seeded "
+                       "synthetic factor values",
+           "operators": len(members), "total_rhs": sum(nrhs), "thread_blocks_per_launch": capi.bf_batch_items(b),
+           "tuned": {"T": cfg["T"], "slot_kb": cfg["slot_kb"], "stages": cfg["stages"],
+                     "candidates": len(cfg.get("tried", []))},
+           "modes": {}}
+    for name, mode in (("each", capi.BF_BATCH_EACH), ("grouped", capi.BF_BATCH_GROUPED),
+                       ("graph", capi.BF_BATCH_GRAPH)):
+        ms = B.time_batch(b, reps=5, mode=mode) + B.time_batch(b, reps=5, mode=mode, adjoint=True)
+        res["modes"][name] = {"ms_apply_plus_adjoint": ms, "vectors_per_s": vecs / (ms / 1e3)}
+    res["graph_vs_each"] = res["modes"]["graph"]["vectors_per_s"] / res["modes"]["each"]["vectors_per_s"]
+    b.destroy()
+    return res
 
 
 def diff_line(dev, stream):
