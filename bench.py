@@ -281,6 +281,18 @@ def run_ours(args, rank, world, local):
                 "note": "useful = 8 real flops per complex multiply-add of the factored operator; issued = "
                         "the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi, Re and Im accumulators) of the dense per-group "
                         "blocks; TF32 peak = measured bf16 dense peak x 1.1/2.25 (nominal TF32/BF16)"}
+        if n == 128 and "tensor" in ent:
+            # precision ladder of the tensor-core core: plain TF32 beside 3xTF32,
+            # each compared with the FP32 CUDA-core fused path on vector 0
+            ref = torch.empty_like(gs[:1])
+            bf.bf_apply(plan, gs[:1], ref, stream=stream)
+            ent["tensor"]["rel_diff_vs_fp32_fused_col0"] = rel_diff(us[:1], ref)
+            bf.bf_plan_set_precision(plan, bf.capi.BF_PREC_TF32)
+            ms_t, _ = timed(gs, us, vs, n, st, 3)
+            bf.bf_apply(plan, gs, us, nrhs=n, stream=stream)
+            ent["tf32"] = {"vectors_per_s": aggregate([ms_t], [2 * n * st * world])[0], "ms_per_step": ms_t / st,
+                           "rel_diff_vs_fp32_fused_col0": rel_diff(us[:1], ref)}
+            bf.bf_plan_set_precision(plan, bf.capi.BF_PREC_FP32)
         sweep_out.append(ent)
         del gs, us, vs
 
@@ -421,6 +433,13 @@ def diff_line(dev, stream):
                    "cross-checked against the plain path; all gradients are checked against the FP64 oracle "
                    "gradient in the GPU tests")
     return res
+
+
+def rel_diff(a, b):
+    """Relative 2-norm difference of two device tensors (host FP64)."""
+    import numpy as np
+    x, y = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128)
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
 
 
 def tf32_peak_tflops():

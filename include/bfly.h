@@ -268,6 +268,18 @@ bf_status bf_diff_forward(bf_diff plan, const bf_dfactors *factors, const void *
 bf_status bf_diff_backward(bf_diff plan, const bf_dfactors *factors, const void *ubar, void *gbar, int nrhs,
                            long long ld, const void *saved, const bf_dgrads *grads, cudaStream_t stream);
 
+/* Precision of the tensor-core multi-RHS core (batches of 32 or more RHS
+ * with r, n0 multiples of 8).  Its MMAs take TF32 operands (the FP32 inputs
+ * truncated to a 10-bit mantissa) with FP32 accumulation; every complex
+ * product is formed from real products.
+ *   BF_PREC_FP32  (default) 3xTF32: a b + a b_lo + a_lo b with x_lo = x - trunc(x),
+ *                 FP32-level results (relative error ~1e-6 against FP64).
+ *   BF_PREC_TF32  one TF32 product per real product: a third of the MMAs and
+ *                 no low parts, relative error ~1e-3.
+ * The fused and CUDA-core paths compute in FP32 whatever is set. */
+typedef enum { BF_PREC_FP32 = 0, BF_PREC_TF32 = 1 } bf_precision;
+bf_status bf_plan_set_precision(bf_plan plan, int precision);
+
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);
 

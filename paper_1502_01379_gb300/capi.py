@@ -23,7 +23,8 @@ EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", 
            "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string",
            "bf_apply_static_scratch", "bf_diff_create", "bf_diff_destroy", "bf_diff_stride",
            "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
-           "bf_batch_check", "bf_batch_items", "bf_batch_destroy")
+           "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision")
+BF_PREC_FP32, BF_PREC_TF32 = 0, 1
 BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
 
@@ -92,6 +93,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                 ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i),
                                 ctypes.POINTER(ll), ctypes.POINTER(bf_batch_config), vp]),
         "bf_batch_apply": (i, [vp, i, i, vp]),
+        "bf_plan_set_precision": (i, [vp, i]),
         "bf_batch_check": (i, [vp, vp]),
         "bf_batch_items": (i, [vp]),
         "bf_batch_destroy": (i, [vp]),
@@ -211,6 +213,11 @@ def bf_apply_adjoint(plan: Plan, x, y, nrhs: int | None = None, ld: int | None =
     xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
     _check(load().bf_apply_adjoint(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi), n, l,
                                    ctypes.c_void_p(_stream_handle(stream))), "bf_apply_adjoint")
+
+
+def bf_plan_set_precision(plan: Plan, precision: int) -> None:
+    """BF_PREC_FP32 (3xTF32, default) or BF_PREC_TF32 for the tensor-core core."""
+    _check(load().bf_plan_set_precision(ctypes.c_void_p(plan.handle), int(precision)), "bf_plan_set_precision")
 
 
 def bf_plan_destroy(plan: Plan) -> None:

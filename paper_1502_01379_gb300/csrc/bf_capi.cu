@@ -83,6 +83,7 @@ struct bf_plan_s {
     bool wide = false, tc = false;           // which multi-RHS cores were built
     int wide_min = 0, tc_min = 0;             // smallest batch each core serves
     int num_sms = 1;
+    int tc_split = 3;                         // tensor-core products: 3 = 3xTF32, 1 = plain TF32
     WideDirection wfwd, wadj;                 // CUDA-core multi-RHS passes
     WideDirection tfwd, tadj;                 // tensor-core multi-RHS passes
     float2 *d_wsA = nullptr;                       // R x nrhs_max pass intermediate
@@ -593,6 +594,40 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of nrhs column-major vectors (16-byte aligned, even ld) as a
+// {2 N floats, nrhs rows} FP32 tensor read in tiles of 32 floats x 128 rows
+// with the 128-byte swizzle; false if it cannot be made.
+bool points_tmap(CUtensorMap *map, const float2 *in, long long N, long long ld, int nrhs) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return false;
+    const cuuint64_t dim[2] = {(cuuint64_t)(2 * N), (cuuint64_t)nrhs};
+    const cuuint64_t stride[1] = {(cuuint64_t)ld * 8};
+    const cuuint32_t box[2] = {32, (cuuint32_t)bftc::NR};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(in), dim, stride, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor-core multi-RHS core: one persistent launch (one CTA per SM) per
 // pass; pass intermediates are stored as 128-RHS tiles [tile][position][128].
 // `in` / `out` must be 16-byte aligned with an even leading dimension.
@@ -627,6 +662,9 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
         p.Kin = wp.Kin;
         p.Nout = wp.Nout;
         p.nrhs = nrhs;
+        p.split = P.tc_split;
+        if (p.load_kind == bftc::LD_POINTS && env_int("BF_TC_TMAP", 1) == 1)
+            p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs) ? 1 : 0;
         const long long items = ntiles * P.m * wp.ngroups;
         const int grid = (int)std::min<long long>(items, P.num_sms);
         bftc::bf_tc_kernel<<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
@@ -1350,6 +1388,13 @@ bf_status bf_batch_check(bf_batch B, cudaStream_t stream) {
 }
 
 int bf_batch_items(bf_batch B) { return B ? B->nitems : 0; }
+
+bf_status bf_plan_set_precision(bf_plan plan, int precision) {
+    if (!plan) return BF_ERR_INVALID;
+    if (precision != BF_PREC_FP32 && precision != BF_PREC_TF32) return BF_ERR_INVALID;
+    plan->tc_split = precision == BF_PREC_TF32 ? 1 : 3;
+    return BF_OK;
+}
 
 bf_status bf_batch_destroy(bf_batch B) {
     if (!B) return BF_OK;

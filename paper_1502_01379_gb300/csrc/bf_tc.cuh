@@ -23,10 +23,16 @@
 // give Re Y = D[:, o] - E[:, Nout+o] and Im Y = D[:, Nout+o] + E[:, o]; the
 // epilogue combines them, so no rearranged copy of F is needed.  Each MMA is
 // 128 x 2 Nout x 8 (kind::tf32, FP32 accumulation).  FP32 accuracy comes from
-// the 3xTF32 split: the tensor core truncates FP32 operands to TF32, so with
-// x_lo = x - trunc(x) every product is formed as a b + a b_lo + a_lo b (the
-// dropped a_lo b_lo is ~2^-22 relative).  X_lo lives next to X in tensor
-// memory; F_lo is built in shared memory by one warp per streamed block.
+// the 3xTF32 split x = x_hi + x_lo with x_hi = x rounded to the nearest TF32
+// value (which the tensor core's truncation leaves unchanged) and
+// x_lo = x - x_hi exactly: every product is formed as
+// a_hi b_hi + a_hi b_lo + a_lo b_hi.  With rounding rather than truncation the
+// low parts take either sign, so the dropped a_lo b_lo (~2^-24 relative) and
+// the truncation of the low parts to TF32 average out over the sums instead
+// of adding up pass after pass.  X_lo lives next to X in tensor memory; the
+// prep warp rounds each streamed F in shared memory and builds F_lo there.
+// A plan may instead ask for plain TF32 products (split = 1: one MMA per
+// product, no low parts), a faster and less accurate rung of the ladder.
 //
 // Tensor memory (512 columns): Re X | Im X | Re X_lo | Im X_lo (64 each) |
 // D (128) | E (128).
@@ -40,8 +46,10 @@
 // (node, group, 128-RHS tile)):
 //  * producer warp: TMA bulk copies of each item's block F into a two-slot
 //    ring and of the item's input tile into a shared-memory staging buffer
-//    (one copy per slot for pass intermediates, one per RHS row for the
-//    input vectors); when it issues item i's copies it also prefetches item
+//    (one copy per slot for pass intermediates; for the input vectors, 2-D
+//    tensor copies of 128 RHS rows x 128 bytes with the 128-byte swizzle, or
+//    one copy per RHS row when no tensor map could be made); when it issues
+//    item i's copies it also prefetches item
 //    i+1's block and tile into L2, so the staging copy of item i+1 (issued
 //    once item i's tile is converted) reads from L2;
 //  * prep warp: F_lo for each ring slot;
@@ -58,6 +66,8 @@
 // expiry the CTA runs its remaining control flow without waiting or
 // computing and the producer drains the copies it issued.
 #pragma once
+
+#include <cuda.h>   // CUtensorMap (type only; the map is encoded through the runtime's driver entry point)
 
 #include "bf_kernels.cuh"
 
@@ -82,7 +92,10 @@ constexpr size_t kSmemBytes = 2ull * kStages * kSlotBytes + kStageBytes + kEpiWa
 enum LoadKind : int { LD_POINTS = 0, LD_SLOTS = 1, LD_GATHER = 2 };
 enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2 };
 
-struct TcParams {
+// Passed as a __grid_constant__ kernel parameter: the TMA reads the tensor
+// map from parameter space.
+struct alignas(64) TcParams {
+    CUtensorMap tmap;       // LD_POINTS with use_tmap: the input vectors as {2 N floats, nrhs rows}
     const float *fac;       // per (node, group): [Re F; Im F], 2 Nout x Kin, K-major no-swizzle
     const float2 *in;       // LD_POINTS: vectors, RHS j at in + j ld_in; else tiles [t][R][re 128 | im 128]
     long long ld_in;
@@ -95,6 +108,8 @@ struct TcParams {
     int a, kb, G, ngroups;  // the group's slots differ in node-slot bits a .. a+kb-1
     int Kin, Nout;
     int nrhs;
+    int split;              // 1: plain TF32 products (a b); 3: 3xTF32 (a b + a b_lo + a_lo b)
+    int use_tmap;           // LD_POINTS: load the tile by tensor-map copies (else one copy per row)
 };
 
 // Byte offset of (row n, col k) in a K-major no-swizzle operand of `rows`
@@ -161,7 +176,10 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // Part of x below the TF32 mantissa (the tensor core truncates the low 13 bits).
-__device__ __forceinline__ float lo_part(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (10-bit mantissa; ties away from zero).
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x00001000u) & 0xFFFFE000u);
+}
 
 struct Smem {
     float *ring, *blo;                 // kStages slots of kSlotBytes each
@@ -206,6 +224,22 @@ __device__ __forceinline__ long long slot_pos(const TcParams &p, const Item &it,
     return ((long long)it.n * p.m + ps) * p.r;
 }
 
+// One 2-D tensor-map tile (TMA) into shared memory, counted on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            bfk::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bfk::smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_tile_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+constexpr uint32_t kBoxBytes = 128u * 128u;   // one tensor-map tile: 128 RHS rows x 128 bytes (16 points)
+
 __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
@@ -231,7 +265,13 @@ __device__ __forceinline__ void tile_copies(const TcParams &p, const Item &w, in
     }
 }
 __device__ __forceinline__ uint32_t tile_bytes(const TcParams &p, const Item &w) {
-    return p.load_kind == LD_POINTS ? (uint32_t)p.Kin * 8u * (uint32_t)w.nt : (uint32_t)p.r * NR * 8u * (uint32_t)p.G;
+    if (p.load_kind == LD_POINTS)
+        return p.use_tmap ? (uint32_t)(p.Kin / 16) * kBoxBytes : (uint32_t)p.Kin * 8u * (uint32_t)w.nt;
+    return (uint32_t)p.r * NR * 8u * (uint32_t)p.G;
+}
+// Tensor-map coordinates of an LD_POINTS item: x (floats) of its first point, y (row) of its first RHS.
+__device__ __forceinline__ int points_x(const TcParams &p, const Item &w) {
+    return (int)(2 * (((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0));
 }
 __device__ __forceinline__ const float *block_src(const TcParams &p, const Item &w) {
     return p.fac + ((long long)w.n * p.ngroups + w.g) * (2ll * p.Nout * p.Kin);
@@ -260,7 +300,10 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
         if (nx > 0 && !warp_wait(s.xfree, (nx - 1) & 1, s.abort_flag, p.err)) break;
         if (lane == 0) bfk::mbar_arrive_expect_tx(s.xfull, tile_bytes(p, w));
         __syncwarp();
-        if (p.load_kind == LD_POINTS)
+        if (p.load_kind == LD_POINTS && p.use_tmap) {
+            if (lane < p.Kin / 16)
+                tma_load_2d(s.xs + (size_t)lane * kBoxBytes, &p.tmap, points_x(p, w) + 32 * lane, w.t * NR, s.xfull);
+        } else if (p.load_kind == LD_POINTS)
             tile_copies(p, w, lane, [&](int i, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + (size_t)i * kPointRow, src, b, s.xfull); });
         else
             tile_copies(p, w, lane, [&](int i, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + (size_t)i * b, src, b, s.xfull); });
@@ -268,7 +311,11 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
         if (item + (int)gridDim.x < nitems) {   // next item of this CTA: into L2
             const Item w2 = decode(p, item + gridDim.x, ntiles);
             if (lane == 0) prefetch_l2(block_src(p, w2), ubytes);
-            tile_copies(p, w2, lane, [&](int, const void *src, uint32_t b) { prefetch_l2(src, b); });
+            if (p.load_kind == LD_POINTS && p.use_tmap) {
+                if (lane < p.Kin / 16) prefetch_tile_2d(&p.tmap, points_x(p, w2) + 32 * lane, w2.t * NR);
+            } else {
+                tile_copies(p, w2, lane, [&](int, const void *src, uint32_t b) { prefetch_l2(src, b); });
+            }
         }
     }
     // Every copy issued must land before the CTA may exit.
@@ -279,7 +326,8 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
     }
 }
 
-// Prep warp: F_lo of each streamed block, in the same operand layout.
+// Prep warp: each streamed block rounded to TF32 in place and its low part
+// F_lo, in the same operand layout.
 __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitems) {
     const int lane = threadIdx.x & 31;
     const int n4 = 2 * p.Nout * p.Kin / 4;
@@ -287,11 +335,14 @@ __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitem
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
         const uint32_t slot = it % kStages;
         if (warp_wait(&s.full[slot], (it / kStages) & 1, s.abort_flag, p.err)) {
-            const float4 *src = reinterpret_cast<const float4 *>(s.ring + (size_t)slot * (kSlotBytes / 4));
-            float4 *dst = reinterpret_cast<float4 *>(s.blo + (size_t)slot * (kSlotBytes / 4));
+            // the block rounded to TF32 in place (the MMAs read it), F_lo = F - round(F)
+            float4 *hi = reinterpret_cast<float4 *>(s.ring + (size_t)slot * (kSlotBytes / 4));
+            float4 *lo = reinterpret_cast<float4 *>(s.blo + (size_t)slot * (kSlotBytes / 4));
             for (int i = lane; i < n4; i += 32) {
-                const float4 v = src[i];
-                dst[i] = make_float4(lo_part(v.x), lo_part(v.y), lo_part(v.z), lo_part(v.w));
+                const float4 v = hi[i];
+                const float4 r = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+                hi[i] = r;
+                if (p.split > 1) lo[i] = make_float4(v.x - r.x, v.y - r.y, v.z - r.z, v.w - r.w);
             }
             fence_async_smem();
         }
@@ -320,13 +371,24 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
             const uint32_t d = tmem + (grp ? kE : kD);
             const uint32_t xh = tmem + (grp ? kXi : kXr), xl = tmem + (grp ? kXil : kXrl);
             if (ok) {
+                // Correction products first, main products last: the tensor core's
+                // FP32 accumulation rounds each step toward zero relative to the
+                // running sum, so the small terms are added while the sum is small
+                // and the large sum sees only Kin/8 accumulation steps.
+                bool first = true;
+                if (p.split > 1) {
+                    for (int kk = 0; kk < p.Kin / 8; ++kk) {
+                        const uint32_t bo = (uint32_t)(2 * kk) * lbo;
+                        const uint32_t c = (uint32_t)(8 * kk);
+                        mma_ts(d, xh + c, sdesc(bl + bo, lbo, 128), idesc, first ? 0u : 1u);
+                        mma_ts(d, xl + c, sdesc(b1 + bo, lbo, 128), idesc, 1);
+                        first = false;
+                    }
+                }
                 for (int kk = 0; kk < p.Kin / 8; ++kk) {
                     const uint32_t bo = (uint32_t)(2 * kk) * lbo;
-                    const uint64_t B = sdesc(b1 + bo, lbo, 128), Bl = sdesc(bl + bo, lbo, 128);
-                    const uint32_t c = (uint32_t)(8 * kk);
-                    mma_ts(d, xh + c, B, idesc, kk > 0 ? 1u : 0u);
-                    mma_ts(d, xh + c, Bl, idesc, 1);
-                    mma_ts(d, xl + c, B, idesc, 1);
+                    mma_ts(d, xh + (uint32_t)(8 * kk), sdesc(b1 + bo, lbo, 128), idesc, first ? 0u : 1u);
+                    first = false;
                 }
             }
             if (grp == 1) mma_commit(&s.empty[slot]);   // ring slot and F_lo free once both groups completed
@@ -343,7 +405,17 @@ __device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32
     const uint32_t ch = part ? kXi : kXr, cl = part ? kXil : kXrl;
     for (int e = hf * half; e < (hf + 1) * half; e += 8) {
         float v[8], vl[8];
-        if (p.load_kind == LD_POINTS) {
+        if (p.load_kind == LD_POINTS && p.use_tmap) {
+            // tile e/16, row mlane (128 B), 16-byte chunk c stored at c ^ (mlane % 8)
+            const unsigned char *row = s.xs + (size_t)(e >> 4) * kBoxBytes + (size_t)mlane * 128;
+            const int c0 = (e & 15) >> 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 q = *reinterpret_cast<const float4 *>(row + (((c0 + i) ^ (mlane & 7)) << 4));
+                v[2 * i] = part ? q.y : q.x;
+                v[2 * i + 1] = part ? q.w : q.z;
+            }
+        } else if (p.load_kind == LD_POINTS) {
             const float4 *row = reinterpret_cast<const float4 *>(s.xs + (size_t)mlane * kPointRow) + (e >> 1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -357,9 +429,13 @@ __device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32
             for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * 2 * NR];
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) vl[i] = lo_part(v[i]);
+        for (int i = 0; i < 8; ++i) {
+            const float hi = tf32_round(v[i]);
+            vl[i] = v[i] - hi;
+            v[i] = hi;
+        }
         tmem_st8(lb + ch + (uint32_t)e, v);
-        tmem_st8(lb + cl + (uint32_t)e, vl);
+        if (p.split > 1) tmem_st8(lb + cl + (uint32_t)e, vl);
     }
     tmem_wait_st();
 }
@@ -437,7 +513,7 @@ __device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const I
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const TcParams p) {
+__global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem s;
     s.ring = reinterpret_cast<float *>(smem_raw);

@@ -301,3 +301,29 @@ def test_full_size_n1m_r16_tensor_core_batch(bf):
     scale = np.linalg.norm(u, axis=1) * np.linalg.norm(f, axis=1)
     assert np.max(np.abs(lhs - rhs) / scale) < TOL
     plan.destroy()
+
+
+def test_precision_ladder_tensor_core(bf):
+    """The tensor-core core's two rungs at N = 2^16, L = 12, r = 16, 128 RHS,
+    against the FP64 C oracle on sampled columns: 3xTF32 (the default) within
+    the FP32 tolerance; plain TF32 (one MMA per product, no low parts) at the
+    error TF32 operands give (relative ~1e-3: well above the FP32 bar, well
+    below 1)."""
+    from bfinputs import complex_normal, synthetic_factors
+    from oracle import capply
+    from paper_1502_01379_gb300 import capi
+    F = synthetic_factors(12, 16, 16, seed=4, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=128)
+    g = complex_normal((128, F.N), seed=8, dtype=np.complex64)
+    P = capply.PreparedFactors(F)
+    ref = [capply.bf_apply_c(P, g[j]) for j in (0, 77, 127)]
+    errs = {}
+    for prec in (capi.BF_PREC_FP32, capi.BF_PREC_TF32):
+        capi.bf_plan_set_precision(plan, prec)
+        u = _run(bf, plan, g)
+        errs[prec] = max(_rel(u[j], r) for j, r in zip((0, 77, 127), ref))
+    assert errs[capi.BF_PREC_FP32] < TOL
+    assert 1e-5 < errs[capi.BF_PREC_TF32] < 1e-2
+    with pytest.raises(capi.BfError):
+        capi.bf_plan_set_precision(plan, 7)
+    plan.destroy()
