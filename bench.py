@@ -61,6 +61,19 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: all-reduce MAX over the default process group
+    (NCCL on the GPUs in a benchmark run; any backend whose tensors live on
+    `device`)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def aggregate(ms_by_rank, vectors_per_rank):
     """Whole-job throughput: all ranks' vectors over the slowest rank's time."""
     ms = max(ms_by_rank)
@@ -204,11 +217,7 @@ def run_ours(args, rank, world, local):
             bf.bf_plan_set_profiling(plan, False)
             kt = bf.bf_plan_kernel_times(plan)
         barrier()
-        ms_all = ms
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_all = float(t.item())
+        ms_all = max_over_ranks(ms, world, dev)
         bf.bf_plan_check(plan)
         return ms_all, kt
 

@@ -1,0 +1,79 @@
+"""bench.py host logic without a GPU: the multi-rank timing reduction on two
+gloo ranks, and the reference arm's JSON line (the FP64 oracle on the small
+workload) with the silence of non-zero ranks."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(10.0 * (rank + 1), world, torch.device("cpu"))
+    value, ms_tot = bench.aggregate([ms], [7 * world])
+    out.put((rank, ms, value, ms_tot))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    """Every rank gets the slowest rank's time; the whole-job value counts all
+    ranks' vectors over that time."""
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, value, ms_tot in res:
+        assert ms == 20.0 and ms_tot == 20.0
+        assert value == pytest.approx(14 / 0.020)
+
+
+def _bench(args, env_extra=None):
+    env = dict(os.environ, **(env_extra or {}))
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True, text=True,
+                          env=env, cwd=ROOT, timeout=600)
+
+
+def test_reference_arm_json_line():
+    r = _bench(["--impl", "reference", "--workload", "fio_n4096_r12", "--steps", "2", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "vectors/s" and d["steps"] == 2 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_other_ranks_exit_silently():
+    r = _bench(["--impl", "reference", "--workload", "fio_n4096_r12", "--steps", "2", "--warmup", "3"],
+               {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_warmup_below_three_is_rejected():
+    r = _bench(["--impl", "reference", "--workload", "fio_n4096_r12", "--steps", "1", "--warmup", "2"])
+    assert r.returncode != 0
