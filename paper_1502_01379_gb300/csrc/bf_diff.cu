@@ -88,6 +88,9 @@ __device__ __forceinline__ void cadd(float2 &a, float2 b) {
 
 // One CTA per unit; RHS in chunks of kChunk.  Shared memory: the unit's
 // parameter blocks, its P-side chunk (count p rows) and Q-side chunk (q rows).
+// GPT: gradient entries per thread (0 for a forward step), so a step's
+// registers, and with them the CTAs per SM, follow its block size.
+template <int GPT>
 __global__ void __launch_bounds__(kThreads) unit_kernel(const Unit a) {
     extern __shared__ float2 sm[];
     const int u = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -99,13 +102,14 @@ __global__ void __launch_bounds__(kThreads) unit_kernel(const Unit a) {
         const int c = e / (a.p * a.q), rem = e - c * a.p * a.q;
         Xs[e] = a.X[(size_t)p_block(a, u, c) * a.p * a.q + rem];
     }
-    const bool grad = a.grad != nullptr;
+    constexpr bool grad = GPT > 0;
+    constexpr int NG = GPT > 0 ? GPT : 1;
     const float2 *pv = a.form == FORM_XH ? a.src : a.ga;
     const float2 *qv = a.form == FORM_X ? a.src : a.gb;
     const bool needP = a.form == FORM_XH || grad, needQ = a.form == FORM_X || grad;
-    float2 acc[kMaxGradPerThread];
+    float2 acc[NG];
 #pragma unroll
-    for (int t = 0; t < kMaxGradPerThread; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int t = 0; t < NG; ++t) acc[t] = make_float2(0.f, 0.f);
     for (int j0 = 0; j0 < a.nrhs; j0 += kChunk) {
         const int nc = min(kChunk, a.nrhs - j0);
         __syncthreads();
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) unit_kernel(const Unit a) {
         }
         if (grad) {                // Xbar_c[row][o] += sum_j P_c[row][j] conj(Q[o][j])
 #pragma unroll
-            for (int t = 0; t < kMaxGradPerThread; ++t) {
+            for (int t = 0; t < NG; ++t) {
                 const int e = tid + t * kThreads;
                 if (e < nx) {
                     const int rr = e / a.q, o = e - rr * a.q;
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) unit_kernel(const Unit a) {
     }
     if (grad) {
 #pragma unroll
-        for (int t = 0; t < kMaxGradPerThread; ++t) {
+        for (int t = 0; t < NG; ++t) {
             const int e = tid + t * kThreads;
             if (e < nx) {
                 const int c = e / (a.p * a.q), rem = e - c * a.p * a.q;
@@ -300,7 +304,11 @@ cudaError_t launch_unit(const Ctx &c, int f, int form, const float2 *src, float2
         nunits = 1LL << (P.L - 1);
     }
     const size_t smem = bfd::unit_smem(a.count, a.p, a.q);
-    bfd::unit_kernel<<<(unsigned)nunits, bfd::kThreads, smem, c.s>>>(a);
+    const int nx = a.count * a.p * a.q;
+    if (!grad) bfd::unit_kernel<0><<<(unsigned)nunits, bfd::kThreads, smem, c.s>>>(a);
+    else if (nx <= 4 * bfd::kThreads) bfd::unit_kernel<4><<<(unsigned)nunits, bfd::kThreads, smem, c.s>>>(a);
+    else if (nx <= 8 * bfd::kThreads) bfd::unit_kernel<8><<<(unsigned)nunits, bfd::kThreads, smem, c.s>>>(a);
+    else bfd::unit_kernel<16><<<(unsigned)nunits, bfd::kThreads, smem, c.s>>>(a);
     return cudaGetLastError();
 }
 
@@ -421,8 +429,14 @@ bf_status bf_diff_create(bf_diff *out, const bf_diff_desc *d) {
     const size_t nvec = 2 + (size_t)(P->k - 1);
     // One attribute value shared by every plan: the opt-in maximum (an upper
     // bound; each launch requests only its unit's shared memory).
-    if (cudaFuncSetAttribute(bfd::unit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(bfd::unit_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(bfd::unit_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(bfd::unit_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(bfd::unit_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess) {
         cudaGetLastError();
         delete P;
         return BF_ERR_CUDA;
