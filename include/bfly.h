@@ -76,9 +76,15 @@ typedef struct bf_plan_s *bf_plan;
 /* Builds a plan: validates the shape, packs the factors into the device
  * layouts of the forward and adjoint kernels (complex64, block-contiguous in
  * the order each thread block consumes them), uploads them, and allocates a
- * workspace of 2^L * r * nrhs_max complex64 entries.  The factor arrays are
- * copied: the caller may free them when this returns.  Synchronizes `stream`
- * before returning.  On error *plan is set to NULL. */
+ * workspace of 2^L * r * nrhs_max complex64 entries.  When nrhs_max >= 8 it
+ * also packs the factors for the CUDA-core multi-RHS core, and when
+ * nrhs_max >= 32 (and r, n0 are multiples of 8 with blocks of at most 64 x 64)
+ * for the tensor-core core -- two levels per pass multiplied out, in FP64,
+ * into dense blocks -- each with its own packed streams and up to three
+ * workspaces of 2^L * r * nrhs_max entries (rounded up to 128 vectors for the
+ * tensor-core core): bf_plan_device_bytes reports the total.  The factor
+ * arrays are copied: the caller may free them when this returns.
+ * Synchronizes `stream` before returning.  On error *plan is set to NULL. */
 bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *factors,
                          cudaStream_t stream);
 
@@ -89,7 +95,10 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
  *            pageable) are staged through plan-owned device buffers, which the
  *            first such call allocates; the host output is complete when
  *            `stream` completes.
- *   nrhs     >= 0; 0 is a no-op.  Processed nrhs_max vectors per pass.
+ *   nrhs     >= 0; 0 is a no-op.  Processed nrhs_max vectors per pass: one
+ *            vector at a time through the fused single-RHS kernels (up to 4
+ *            per thread block), 8..31 through the CUDA-core multi-RHS core,
+ *            32 or more through the tensor-core core (bf_plan_set_precision).
  * in and out must not overlap (BF_ERR_INVALID).  One plan owns one
  * workspace: calls on the same plan must not run concurrently on different
  * streams. */

@@ -629,8 +629,9 @@ bool points_tmap(CUtensorMap *map, const float2 *in, long long N, long long ld, 
 }
 
 // Tensor-core multi-RHS core: one persistent launch (one CTA per SM) per
-// pass; pass intermediates are stored as 128-RHS tiles [tile][position][128].
-// `in` / `out` must be 16-byte aligned with an even leading dimension.
+// pass; pass intermediates are 128-RHS tiles, position-major and planar
+// ([tile][position][re 128 | im 128]).  `in` / `out` must be 16-byte aligned
+// with an even leading dimension.
 cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *in, long long ld_in, float2 *out,
                       long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
     float2 *buf[2] = {P.d_wsA, P.d_ws};

@@ -52,7 +52,6 @@ struct WideParams {
     int a, kb;              // the group's slots differ in node-slot bits a .. a+kb-1
     int ngroups;
     int nrhs, stages, slot_len;
-    int in_t, out_t;        // tensor-core path: 1 = intermediate stored [position][RHS] (ld = position stride)
     Level lev[bfk::kMaxLevels];   // MERGE / SPLIT: lev.s holds the local slot bit
 };
 
