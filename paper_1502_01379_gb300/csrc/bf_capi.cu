@@ -84,6 +84,7 @@ struct bf_plan_s {
     int wide_min = 0, tc_min = 0;             // smallest batch each core serves
     int num_sms = 1;
     int tc_split = 3;                         // tensor-core products: 3 = 3xTF32, 1 = plain TF32
+    int inject_stall = 0;                     // failure-detection test hook (BF_INJECT_STALL=1 at creation)
     WideDirection wfwd, wadj;                 // CUDA-core multi-RHS passes
     WideDirection tfwd, tadj;                 // tensor-core multi-RHS passes
     float2 *d_wsA = nullptr;                       // R x nrhs_max pass intermediate
@@ -730,6 +731,7 @@ Params base_params(const bf_plan_s &P, const Stream &st) {
     p.fac = st.d;
     p.cta_len = st.cta_len;
     p.err = P.d_err;
+    p.stall = P.inject_stall;
     p.nlev = st.nlev;
     for (int i = 0; i < st.nlev; ++i) p.lev[i] = st.lev[i];
     p.m = P.m;
@@ -984,6 +986,7 @@ bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, c
     // Defaults measured on GB300 at N = 2^20, r = 16: 256 consumers, 64 KB
     // slots and as many slots as fit (2 there) stream at the HBM copy rate.
     P->consumers = cfg.consumers;
+    P->inject_stall = env_int("BF_INJECT_STALL", 0) == 1 ? 1 : 0;
     int slot_len = cfg.slot_kb * 128;
     slot_len = std::max(slot_len, std::max(4 * r * r, n0 * r + 1));
     P->slot_len = (slot_len + 1) & ~1;

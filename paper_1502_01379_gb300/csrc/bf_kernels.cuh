@@ -67,6 +67,7 @@ struct Params {
     int nrhs;               // vectors in this launch
     int stages;             // ring depth
     int slot_len;           // complex elements per ring slot
+    int stall;              // failure-detection test hook: the producer issues no copies
     Level lev[kMaxLevels];
 };
 
@@ -176,9 +177,15 @@ __device__ __forceinline__ void produce_drain(const P &p, uint32_t gs, uint64_t 
 }
 
 // One thread streams this CTA's factor chunk, stage by stage, into the ring.
+// With the stall hook set it issues nothing: every consumer wait then runs
+// into its bound and the launch ends with the error word set.
+__device__ __forceinline__ bool stalled(const Params &p) { return p.stall != 0; }
+template <class P>
+__device__ __forceinline__ bool stalled(const P &) { return false; }
 template <class P>
 __device__ __forceinline__ void produce(const P &p, long long chunk, float2 *ring, uint64_t *full, uint64_t *empty,
                                        volatile int *abort_flag) {
+    if (stalled(p)) return;
     uint32_t gs = 0;
     produce_chunk(p, chunk, gs, ring, full, empty, abort_flag);
     produce_drain(p, gs, full, abort_flag);

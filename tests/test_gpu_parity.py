@@ -327,3 +327,43 @@ def test_precision_ladder_tensor_core(bf):
     with pytest.raises(capi.BfError):
         capi.bf_plan_set_precision(plan, 7)
     plan.destroy()
+
+
+def test_bounded_wait_expiry_reports_timeout_and_context_survives(bf, monkeypatch):
+    """Failure detection without a GPU fault: with the stall hook the fused
+    kernels' producer issues no copies, every consumer wait runs into its
+    bound (about 2 s), the launch ends with the error word set, and
+    bf_plan_check reports BF_ERR_TIMEOUT.  The context stays usable: a plan
+    created afterwards computes the right result."""
+    from bfinputs import complex_normal, synthetic_factors
+    monkeypatch.setenv("BF_INJECT_STALL", "1")
+    F = synthetic_factors(6, 4, 5, seed=3, dtype=np.complex64)
+    stalled = bf.bf_plan_create(F, nrhs_max=1)
+    monkeypatch.delenv("BF_INJECT_STALL")
+    g = complex_normal((1, F.N), seed=4, dtype=np.complex64)
+    x = torch.from_numpy(g).cuda()
+    y = torch.empty_like(x)
+    bf.bf_apply(stalled, x, y)
+    torch.cuda.synchronize()
+    with pytest.raises(bf.BfError) as err:
+        bf.bf_plan_check(stalled)
+    assert err.value.status == bf.BF_ERR_TIMEOUT
+    bf.bf_plan_check(stalled)          # the error word was cleared
+    stalled.destroy()
+    plan = bf.bf_plan_create(F, nrhs_max=1)
+    assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+    plan.destroy()
+
+
+def test_workspace_allocation_failure_is_reported(bf):
+    """A workspace the GPU cannot hold is refused with BF_ERR_NOMEM, the
+    partial plan is released, and the next plan works."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(8, 16, 16, seed=5, dtype=np.complex64)
+    with pytest.raises(bf.BfError) as err:
+        bf.bf_plan_create(F, nrhs_max=1 << 26)      # 2^8 r x 2^26 vectors x 8 B = 2 TB of workspace
+    assert err.value.status == bf.BF_ERR_NOMEM
+    g = complex_normal((3, F.N), seed=6, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=3)
+    assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+    plan.destroy()
