@@ -291,16 +291,20 @@ def run_ours(args, rank, world, local):
                         "the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi, Re and Im accumulators) of the dense per-group "
                         "blocks; TF32 peak = measured bf16 dense peak x 1.1/2.25 (nominal TF32/BF16)"}
         if n == 128 and "tensor" in ent:
-            # precision ladder of the tensor-core core: plain TF32 beside 3xTF32,
+            # precision ladder of the tensor-core core: the other rungs beside 3xTF32,
             # each compared with the FP32 CUDA-core fused path on vector 0
             ref = torch.empty_like(gs[:1])
             bf.bf_apply(plan, gs[:1], ref, stream=stream)
             ent["tensor"]["rel_diff_vs_fp32_fused_col0"] = rel_diff(us[:1], ref)
-            bf.bf_plan_set_precision(plan, bf.capi.BF_PREC_TF32)
-            ms_t, _ = timed(gs, us, vs, n, st, 3)
-            bf.bf_apply(plan, gs, us, nrhs=n, stream=stream)
-            ent["tf32"] = {"vectors_per_s": aggregate([ms_t], [2 * n * st * world])[0], "ms_per_step": ms_t / st,
-                           "rel_diff_vs_fp32_fused_col0": rel_diff(us[:1], ref)}
+            for name, prec in (("tf32", bf.capi.BF_PREC_TF32), ("bf16x6", bf.capi.BF_PREC_BF16X6),
+                               ("bf16x3", bf.capi.BF_PREC_BF16X3), ("bf16", bf.capi.BF_PREC_BF16)):
+                bf.bf_plan_set_precision(plan, prec)
+                ms_t, kt_t = timed(gs, us, vs, n, st, 3, profile=True)
+                bf.bf_apply(plan, gs, us, nrhs=n, stream=stream)
+                launches = kt_t["down"][0]
+                ent[name] = {"vectors_per_s": aggregate([ms_t], [2 * n * st * world])[0], "ms_per_step": ms_t / st,
+                             "apply_ms": (kt_t["down"][1] + kt_t["up"][1]) / launches,
+                             "rel_diff_vs_fp32_fused_col0": rel_diff(us[:1], ref)}
             bf.bf_plan_set_precision(plan, bf.capi.BF_PREC_FP32)
         sweep_out.append(ent)
         del gs, us, vs

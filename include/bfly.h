@@ -278,15 +278,31 @@ bf_status bf_diff_backward(bf_diff plan, const bf_dfactors *factors, const void 
                            long long ld, const void *saved, const bf_dgrads *grads, cudaStream_t stream);
 
 /* Precision of the tensor-core multi-RHS core (batches of 32 or more RHS
- * with r, n0 multiples of 8).  Its MMAs take TF32 operands (the FP32 inputs
- * truncated to a 10-bit mantissa) with FP32 accumulation; every complex
- * product is formed from real products.
- *   BF_PREC_FP32  (default) 3xTF32: a b + a b_lo + a_lo b with x_lo = x - trunc(x),
- *                 FP32-level results (relative error ~1e-6 against FP64).
- *   BF_PREC_TF32  one TF32 product per real product: a third of the MMAs and
- *                 no low parts, relative error ~1e-3.
- * The fused and CUDA-core paths compute in FP32 whatever is set. */
-typedef enum { BF_PREC_FP32 = 0, BF_PREC_TF32 = 1 } bf_precision;
+ * with r, n0 multiples of 8).  Its MMAs take TF32 or BF16 operands with FP32
+ * accumulation; every complex product is formed from real products.  A
+ * split rung writes each FP32 value x as x_hi + x_lo, x_hi = x rounded to the
+ * nearest value of the operand type, x_lo = x - x_hi (rounded again), and
+ * forms a b as a_lo b_hi + a_hi b_lo + a_hi b_hi (three MMAs, small terms
+ * first).  Errors are relative 2-norm errors against the FP64 apply of the
+ * same factors (N = 2^16 .. 2^20, r = 16, 128 RHS).
+ *   BF_PREC_FP32    (default) 3xTF32 (K = 8 per MMA): ~1e-6.
+ *   BF_PREC_TF32    one TF32 product: a third of the MMAs, ~1e-3.
+ *   BF_PREC_BF16X6  BF16 three-way split x = hi + mid + lo (24 mantissa bits),
+ *                   six BF16 MMAs of K = 16 per product (the terms down to
+ *                   2^-16): as many MMAs as 3xTF32, ~1e-6.
+ *   BF_PREC_BF16X3  BF16 hi/lo split (16 mantissa bits): half the MMAs of
+ *                   3xTF32, ~1e-5.
+ *   BF_PREC_BF16    one BF16 product: a sixth of the MMAs of 3xTF32, ~6e-3.
+ * BF16 shares FP32's exponent range, so no scaling is applied.  The fused and
+ * CUDA-core paths compute in FP32 whatever is set.  BF_ERR_INVALID for any
+ * other value. */
+typedef enum {
+    BF_PREC_FP32 = 0,
+    BF_PREC_TF32 = 1,
+    BF_PREC_BF16X3 = 2,
+    BF_PREC_BF16 = 3,
+    BF_PREC_BF16X6 = 4
+} bf_precision;
 bf_status bf_plan_set_precision(bf_plan plan, int precision);
 
 /* Static text for a status code. */

@@ -24,7 +24,7 @@ EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", 
            "bf_apply_static_scratch", "bf_diff_create", "bf_diff_destroy", "bf_diff_stride",
            "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
            "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision")
-BF_PREC_FP32, BF_PREC_TF32 = 0, 1
+BF_PREC_FP32, BF_PREC_TF32, BF_PREC_BF16X3, BF_PREC_BF16, BF_PREC_BF16X6 = 0, 1, 2, 3, 4
 BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
 
@@ -216,7 +216,9 @@ def bf_apply_adjoint(plan: Plan, x, y, nrhs: int | None = None, ld: int | None =
 
 
 def bf_plan_set_precision(plan: Plan, precision: int) -> None:
-    """BF_PREC_FP32 (3xTF32, default) or BF_PREC_TF32 for the tensor-core core."""
+    """Operand precision of the tensor-core core: BF_PREC_FP32 (3xTF32, the
+    default), BF_PREC_TF32, BF_PREC_BF16X6 (BF16 hi/mid/lo split),
+    BF_PREC_BF16X3 (BF16 hi/lo split) or BF_PREC_BF16."""
     _check(load().bf_plan_set_precision(ctypes.c_void_p(plan.handle), int(precision)), "bf_plan_set_precision")
 
 

@@ -48,6 +48,8 @@ struct WidePass {
     int load_kind = 0, store_kind = 0;
     int a = 0, kb = 0, G = 1, ngroups = 1;
     int Kin = 0, Nout = 0;   // tensor-core core: dense block per (node, group), Nout x Kin complex
+    uint16_t *d16 = nullptr; // tensor-core core, BF16 rungs: the blocks split into d16_parts BF16 parts
+    int d16_parts = 0;
 };
 
 // Configuration of one multi-RHS core: CUDA-core (bf_wide.cuh) or tensor-core (bf_tc.cuh).
@@ -83,7 +85,8 @@ struct bf_plan_s {
     bool wide = false, tc = false;           // which multi-RHS cores were built
     int wide_min = 0, tc_min = 0;             // smallest batch each core serves
     int num_sms = 1;
-    int tc_split = 3;                         // tensor-core products: 3 = 3xTF32, 1 = plain TF32
+    int tc_split = 3;                         // tensor-core products per real product: 1 plain, 3 hi/lo, 6 hi/mid/lo
+    int tc_bf16 = 0;                          // tensor-core operand type: 0 = TF32, 1 = BF16
     int inject_stall = 0;                     // failure-detection test hook (BF_INJECT_STALL=1 at creation)
     WideDirection wfwd, wadj;                 // CUDA-core multi-RHS passes
     WideDirection tfwd, tadj;                 // tensor-core multi-RHS passes
@@ -644,6 +647,7 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
         bftc::TcParams p;
         std::memset(&p, 0, sizeof(p));
         p.fac = reinterpret_cast<const float *>(wp.st.d);
+        p.fac16 = wp.d16;
         p.in = ps == 0 ? in : buf[(ps - 1) & 1];
         p.ld_in = ps == 0 ? ld_in : 0;
         p.out = ps == np - 1 ? out : buf[ps & 1];
@@ -665,6 +669,7 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
         p.Nout = wp.Nout;
         p.nrhs = nrhs;
         p.split = P.tc_split;
+        p.bf16 = P.tc_bf16;
         if (p.load_kind == bftc::LD_POINTS && env_int("BF_TC_TMAP", 1) == 1)
             p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs) ? 1 : 0;
         const long long items = ntiles * P.m * wp.ngroups;
@@ -710,7 +715,10 @@ void free_plan(bf_plan_s *P) {
         cudaFree(d->d_S);
     }
     for (WideDirection *d : {&P->wfwd, &P->wadj, &P->tfwd, &P->tadj})
-        for (auto &wp : d->pass) cudaFree(wp.st.d);
+        for (auto &wp : d->pass) {
+            cudaFree(wp.st.d);
+            cudaFree(wp.d16);
+        }
     cudaFree(P->d_wsA);
     cudaFree(P->d_ws);
     cudaFree(P->d_stage_in);
@@ -1393,10 +1401,62 @@ bf_status bf_batch_check(bf_batch B, cudaStream_t stream) {
 
 int bf_batch_items(bf_batch B) { return B ? B->nitems : 0; }
 
+// The tensor-core blocks of both directions split into `parts` BF16 parts
+// (0: none kept).  All new buffers are allocated before anything is
+// released, so on BF_ERR_NOMEM the plan is unchanged.  Synchronous: the
+// splits run on the legacy default stream and are waited for.
+static bf_status set_bf16_blocks(bf_plan_s &P, int parts) {
+    std::vector<WidePass *> todo;
+    for (WideDirection *D : {&P.tfwd, &P.tadj})
+        for (auto &wp : D->pass)
+            if (wp.d16_parts != parts) todo.push_back(&wp);
+    if (todo.empty()) return BF_OK;
+    auto part_bytes = [&](const WidePass &wp) {
+        return (size_t)P.m * wp.ngroups * 2 * wp.Nout * wp.Kin * sizeof(uint16_t);
+    };
+    std::vector<uint16_t *> fresh(todo.size(), nullptr);
+    if (parts > 0)
+        for (size_t i = 0; i < todo.size(); ++i)
+            if (cudaMalloc(&fresh[i], part_bytes(*todo[i]) * parts) != cudaSuccess) {
+                cudaGetLastError();
+                for (uint16_t *q : fresh) cudaFree(q);
+                return BF_ERR_NOMEM;
+            }
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaErrorUnknown);   // no launch reads the old parts
+    for (size_t i = 0; i < todo.size(); ++i) {
+        WidePass &wp = *todo[i];
+        cudaFree(wp.d16);
+        P.device_bytes -= part_bytes(wp) * wp.d16_parts;
+        wp.d16 = fresh[i];
+        wp.d16_parts = parts;
+        if (parts == 0) continue;
+        P.device_bytes += part_bytes(wp) * parts;
+        const long long nblocks = (long long)P.m * wp.ngroups;
+        const long long chunks = nblocks * 2 * wp.Nout * wp.Kin / 8;
+        const int grid = (int)std::min<long long>((chunks + 255) / 256, 8LL * P.num_sms);
+        bftc::bf16_split_kernel<<<grid, 256>>>(reinterpret_cast<const float *>(wp.st.d),
+                                               reinterpret_cast<uint4 *>(wp.d16), nblocks, 2 * wp.Nout, wp.Kin, parts);
+        if (cudaGetLastError() != cudaSuccess) return cuda_fail(cudaErrorLaunchFailure);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    return BF_OK;
+}
+
 bf_status bf_plan_set_precision(bf_plan plan, int precision) {
     if (!plan) return BF_ERR_INVALID;
-    if (precision != BF_PREC_FP32 && precision != BF_PREC_TF32) return BF_ERR_INVALID;
-    plan->tc_split = precision == BF_PREC_TF32 ? 1 : 3;
+    int split, bf16;
+    switch (precision) {
+    case BF_PREC_FP32: split = 3; bf16 = 0; break;
+    case BF_PREC_TF32: split = 1; bf16 = 0; break;
+    case BF_PREC_BF16X3: split = 3; bf16 = 1; break;
+    case BF_PREC_BF16: split = 1; bf16 = 1; break;
+    case BF_PREC_BF16X6: split = 6; bf16 = 1; break;
+    default: return BF_ERR_INVALID;
+    }
+    const bf_status st = set_bf16_blocks(*plan, bf16 ? (split == 6 ? 3 : split == 3 ? 2 : 1) : 0);
+    if (st != BF_OK) return st;
+    plan->tc_split = split;
+    plan->tc_bf16 = bf16;
     return BF_OK;
 }
 

@@ -35,7 +35,9 @@
 // product, no low parts), a faster and less accurate rung of the ladder.
 //
 // Tensor memory (512 columns): Re X | Im X | Re X_lo | Im X_lo (64 each) |
-// D (128) | E (128).
+// D (128) | E (128).  BF16 operands pack two values per column, so each X
+// part needs Kin/2 <= 32 columns; the three-way split keeps X_mid in the
+// upper 32 columns of the X_hi range.
 //
 // Pass intermediates are 128-RHS tiles stored position-major and planar:
 // position pos of tile t holds the 128 real parts, then the 128 imaginary
@@ -68,6 +70,7 @@
 #pragma once
 
 #include <cuda.h>   // CUtensorMap (type only; the map is encoded through the runtime's driver entry point)
+#include <cuda_bf16.h>
 
 #include "bf_kernels.cuh"
 
@@ -97,6 +100,8 @@ enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2 };
 struct alignas(64) TcParams {
     CUtensorMap tmap;       // LD_POINTS with use_tmap: the input vectors as {2 N floats, nrhs rows}
     const float *fac;       // per (node, group): [Re F; Im F], 2 Nout x Kin, K-major no-swizzle
+    const uint16_t *fac16;  // BF16 rungs: per (node, group) the split parts (hi, then lo or mid, lo) of
+                            // the same block, each 2 Nout x Kin BF16 in the 8-element core-row layout
     const float2 *in;       // LD_POINTS: vectors, RHS j at in + j ld_in; else tiles [t][R][re 128 | im 128]
     long long ld_in;
     float2 *out;            // ST_POINTS: vectors, RHS j at out + j ld_out; else tiles [t][R][re 128 | im 128]
@@ -108,7 +113,8 @@ struct alignas(64) TcParams {
     int a, kb, G, ngroups;  // the group's slots differ in node-slot bits a .. a+kb-1
     int Kin, Nout;
     int nrhs;
-    int split;              // 1: plain TF32 products (a b); 3: 3xTF32 (a b + a b_lo + a_lo b)
+    int split;              // products per real product: 1 plain; 3 hi/lo split; 6 (BF16 only) hi/mid/lo split
+    int bf16;               // operand type: 0 TF32 (kind::tf32, K = 8), 1 BF16 (kind::f16, K = 16)
     int use_tmap;           // LD_POINTS: load the tile by tensor-map copies (else one copy per row)
 };
 
@@ -133,6 +139,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 // kind::tf32, FP32 accumulator, A and B K-major, N = n, M = 128.
 __device__ __forceinline__ uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(NR >> 4) << 24);
+}
+// kind::f16 with A and B both BF16, FP32 accumulator, K-major, N = n, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(NR >> 4) << 24);
+}
+// D[tmem] (+)= A[tmem] * B[smem], BF16 operands (K = 16)
+__device__ __forceinline__ void mma_ts_bf16(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
 }
 // D[tmem] (+)= A[tmem] * B[smem]
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -174,11 +191,55 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
                  "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
                  : "memory");
 }
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // Part of x below the TF32 mantissa (the tensor core truncates the low 13 bits).
 // x rounded to the nearest TF32 value (10-bit mantissa; ties away from zero).
 __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x00001000u) & 0xFFFFE000u);
+}
+// x rounded to the nearest BF16 value (ties away from zero), as FP32 bits
+// whose low 16 bits are zero: two integer ALU operations.
+__device__ __forceinline__ uint32_t bf16_hi_bits(float x) { return (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u; }
+// Two values rounded to BF16 (to nearest even) and packed, a in the low half
+// (the lower K index of an operand pair): one conversion instruction.
+__device__ __forceinline__ uint32_t pack_bf16_rn(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+// The splits below take the high (and middle) parts by integer rounding and
+// only the last part by a conversion, so the work is shared between the
+// integer and conversion pipes; every difference is exact in FP32.
+// Eight values -> BF16 pairs: x rounded (plain rung).
+__device__ __forceinline__ void round_bf16x8(const float (&v)[8], uint32_t (&hi)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) hi[i] = pack_bf16_rn(v[2 * i], v[2 * i + 1]);
+}
+// Eight values -> BF16 high parts (x rounded) and low parts (x - hi, rounded): 16 mantissa bits.
+__device__ __forceinline__ void split_bf16x8(const float (&v)[8], uint32_t (&hi)[4], uint32_t (&lo)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t h0 = bf16_hi_bits(v[2 * i]), h1 = bf16_hi_bits(v[2 * i + 1]);
+        hi[i] = __byte_perm(h0, h1, 0x7632);
+        lo[i] = pack_bf16_rn(v[2 * i] - __uint_as_float(h0), v[2 * i + 1] - __uint_as_float(h1));
+    }
+}
+// Three-way split x = hi + mid + lo: 24 mantissa bits.
+__device__ __forceinline__ void split3_bf16x8(const float (&v)[8], uint32_t (&hi)[4], uint32_t (&mid)[4],
+                                              uint32_t (&lo)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t h0 = bf16_hi_bits(v[2 * i]), h1 = bf16_hi_bits(v[2 * i + 1]);
+        const float r0 = v[2 * i] - __uint_as_float(h0), r1 = v[2 * i + 1] - __uint_as_float(h1);
+        const uint32_t m0 = bf16_hi_bits(r0), m1 = bf16_hi_bits(r1);
+        hi[i] = __byte_perm(h0, h1, 0x7632);
+        mid[i] = __byte_perm(m0, m1, 0x7632);
+        lo[i] = pack_bf16_rn(r0 - __uint_as_float(m0), r1 - __uint_as_float(m1));
+    }
 }
 
 struct Smem {
@@ -276,13 +337,23 @@ __device__ __forceinline__ int points_x(const TcParams &p, const Item &w) {
 __device__ __forceinline__ const float *block_src(const TcParams &p, const Item &w) {
     return p.fac + ((long long)w.n * p.ngroups + w.g) * (2ll * p.Nout * p.Kin);
 }
+// BF16 rungs: split parts per block and bytes per part.
+__device__ __forceinline__ int bf16_parts(const TcParams &p) { return p.split == 6 ? 3 : p.split == 3 ? 2 : 1; }
+__device__ __forceinline__ uint32_t part_bytes(const TcParams &p) { return 2u * p.Nout * p.Kin * 2u; }
+__device__ __forceinline__ const uint16_t *block_src16(const TcParams &p, const Item &w) {
+    return p.fac16 + ((long long)w.n * p.ngroups + w.g) * (2ll * p.Nout * p.Kin) * bf16_parts(p);
+}
+// Bytes of one item's block as streamed: FP32, or the BF16 parts.
+__device__ __forceinline__ uint32_t block_bytes(const TcParams &p) {
+    return p.bf16 ? part_bytes(p) * (uint32_t)bf16_parts(p) : 2u * p.Nout * p.Kin * 4u;
+}
 
 // Producer warp: the item's block F into ring slot (it % kStages), then its
 // input tile into the staging buffer once the epilogue warps have converted
 // the previous one; with the copies of item i, L2 prefetches of item i+1.
 __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int ntiles, int nitems) {
     const int lane = threadIdx.x & 31;
-    const uint32_t ubytes = 2u * p.Nout * p.Kin * 4u;
+    const uint32_t ubytes = block_bytes(p);
     uint32_t nf = 0, nx = 0;   // factor copies / staging groups issued
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const Item w = decode(p, item, ntiles);
@@ -292,7 +363,16 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
             ok = !*s.abort_flag && (use == 0 || bfk::mbar_wait(&s.empty[slot], (use - 1) & 1, s.abort_flag, p.err));
             if (ok) {
                 bfk::mbar_arrive_expect_tx(&s.full[slot], ubytes);
-                bfk::bulk_g2s(s.ring + (size_t)slot * (kSlotBytes / 4), block_src(p, w), ubytes, &s.full[slot]);
+                if (!p.bf16) {
+                    bfk::bulk_g2s(s.ring + (size_t)slot * (kSlotBytes / 4), block_src(p, w), ubytes, &s.full[slot]);
+                } else {   // parts 0, 1 into the ring slot, part 2 (three-way split) into the second buffer
+                    const uint32_t pb = part_bytes(p), n01 = min(ubytes, 2u * pb);
+                    bfk::bulk_g2s(s.ring + (size_t)slot * (kSlotBytes / 4), block_src16(p, w), n01, &s.full[slot]);
+                    if (ubytes > n01)
+                        bfk::bulk_g2s(s.blo + (size_t)slot * (kSlotBytes / 4),
+                                      reinterpret_cast<const unsigned char *>(block_src16(p, w)) + n01, ubytes - n01,
+                                      &s.full[slot]);
+                }
             }
         }
         if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0) == 0) break;
@@ -310,7 +390,7 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
         ++nx;
         if (item + (int)gridDim.x < nitems) {   // next item of this CTA: into L2
             const Item w2 = decode(p, item + gridDim.x, ntiles);
-            if (lane == 0) prefetch_l2(block_src(p, w2), ubytes);
+            if (lane == 0) prefetch_l2(p.bf16 ? (const void *)block_src16(p, w2) : (const void *)block_src(p, w2), ubytes);
             if (p.load_kind == LD_POINTS && p.use_tmap) {
                 if (lane < p.Kin / 16) prefetch_tile_2d(&p.tmap, points_x(p, w2) + 32 * lane, w2.t * NR);
             } else {
@@ -334,7 +414,8 @@ __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitem
     uint32_t it = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
         const uint32_t slot = it % kStages;
-        if (warp_wait(&s.full[slot], (it / kStages) & 1, s.abort_flag, p.err)) {
+        const bool ok = warp_wait(&s.full[slot], (it / kStages) & 1, s.abort_flag, p.err);
+        if (ok && !p.bf16) {   // (BF16 rungs stream blocks already split: nothing to do)
             // the block rounded to TF32 in place (the MMAs read it), F_lo = F - round(F)
             float4 *hi = reinterpret_cast<float4 *>(s.ring + (size_t)slot * (kSlotBytes / 4));
             float4 *lo = reinterpret_cast<float4 *>(s.blo + (size_t)slot * (kSlotBytes / 4));
@@ -370,7 +451,44 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
             }
             const uint32_t d = tmem + (grp ? kE : kD);
             const uint32_t xh = tmem + (grp ? kXi : kXr), xl = tmem + (grp ? kXil : kXrl);
-            if (ok) {
+            if (ok && p.bf16 && p.split == 6) {
+                // BF16 three-way split: the terms of order 2^-16 (hi lo, lo hi, mid mid),
+                // then 2^-8 (hi mid, mid hi), then hi hi.  X_mid sits 32 columns after X_hi.
+                const uint32_t pb = 2u * p.Nout * p.Kin * 2u;
+                const uint32_t idesc16 = idesc_bf16(rows), bhi = b1, bmid = b1 + pb, blow = bl;
+                const int nk = p.Kin / 16;
+                for (int kk = 0; kk < nk; ++kk) {
+                    const uint32_t bo = (uint32_t)(2 * kk) * lbo, c = (uint32_t)(8 * kk);
+                    mma_ts_bf16(d, xh + c, sdesc(blow + bo, lbo, 128), idesc16, kk ? 1u : 0u);
+                    mma_ts_bf16(d, xl + c, sdesc(bhi + bo, lbo, 128), idesc16, 1);
+                    mma_ts_bf16(d, xh + 32 + c, sdesc(bmid + bo, lbo, 128), idesc16, 1);
+                }
+                for (int kk = 0; kk < nk; ++kk) {
+                    const uint32_t bo = (uint32_t)(2 * kk) * lbo, c = (uint32_t)(8 * kk);
+                    mma_ts_bf16(d, xh + c, sdesc(bmid + bo, lbo, 128), idesc16, 1);
+                    mma_ts_bf16(d, xh + 32 + c, sdesc(bhi + bo, lbo, 128), idesc16, 1);
+                }
+                for (int kk = 0; kk < nk; ++kk)
+                    mma_ts_bf16(d, xh + (uint32_t)(8 * kk), sdesc(bhi + (uint32_t)(2 * kk) * lbo, lbo, 128), idesc16, 1);
+            } else if (ok && p.bf16) {
+                // BF16: K = 16 per MMA; F_hi, F_lo consecutive in the ring slot
+                const uint32_t idesc16 = idesc_bf16(rows), bhi = b1, blow = b1 + 2u * p.Nout * p.Kin * 2u;
+                bool first = true;
+                if (p.split > 1) {
+                    for (int kk = 0; kk < p.Kin / 16; ++kk) {
+                        const uint32_t bo = (uint32_t)(2 * kk) * lbo;
+                        const uint32_t c = (uint32_t)(8 * kk);
+                        mma_ts_bf16(d, xh + c, sdesc(blow + bo, lbo, 128), idesc16, first ? 0u : 1u);
+                        mma_ts_bf16(d, xl + c, sdesc(bhi + bo, lbo, 128), idesc16, 1);
+                        first = false;
+                    }
+                }
+                for (int kk = 0; kk < p.Kin / 16; ++kk) {
+                    const uint32_t bo = (uint32_t)(2 * kk) * lbo;
+                    mma_ts_bf16(d, xh + (uint32_t)(8 * kk), sdesc(bhi + bo, lbo, 128), idesc16, first ? 0u : 1u);
+                    first = false;
+                }
+            } else if (ok) {
                 // Correction products first, main products last: the tensor core's
                 // FP32 accumulation rounds each step toward zero relative to the
                 // running sum, so the small terms are added while the sum is small
@@ -427,6 +545,20 @@ __device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32
             const float *col = reinterpret_cast<const float *>(s.xs) + (size_t)e * 2 * NR + part * NR + mlane;
 #pragma unroll
             for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * 2 * NR];
+        }
+        if (p.bf16) {   // BF16 pairs: element e + 2i in the low half of column (e / 2) + i
+            uint32_t h[4], m[4], l[4];
+            if (p.split == 6) {
+                split3_bf16x8(v, h, m, l);
+                tmem_st4(lb + ch + 32 + (uint32_t)(e >> 1), m);   // X_mid 32 columns after X_hi
+            } else if (p.split == 3) {
+                split_bf16x8(v, h, l);
+            } else {
+                round_bf16x8(v, h);
+            }
+            tmem_st4(lb + ch + (uint32_t)(e >> 1), h);
+            if (p.split > 1) tmem_st4(lb + cl + (uint32_t)(e >> 1), l);
+            continue;
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -510,6 +642,40 @@ __device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const I
                 dst[(size_t)i * 2 * NR + NR] = im[i];
             }
         }
+    }
+}
+
+// The blocks of one tensor-core pass split for a BF16 rung, once per plan
+// and rung: block b's FP32 [Re F; Im F] (rows = 2 Nout, the layout of boff)
+// becomes its `parts` BF16 parts (hi; hi, lo; or hi, mid, lo), each in the
+// 8-element core-row layout the MMAs read, so the kernel streams them as
+// they are.  One 16-byte chunk (8 values of one row) of every part per
+// thread; chunk c of a part is K chunk c / rows of row c % rows, whose 8
+// values are the FP32 layout's chunks 2 kc rows + n and (2 kc + 1) rows + n.
+__global__ void bf16_split_kernel(const float *fac, uint4 *out, long long nblocks, int rows, int Kin, int parts) {
+    const long long per = (long long)rows * Kin / 8;
+    const long long total = nblocks * per;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / per;
+        const int c = (int)(i - b * per);
+        const int kc = c / rows, n = c - kc * rows;
+        const float4 *src = reinterpret_cast<const float4 *>(fac + b * rows * Kin);
+        const float4 x = src[(2 * kc) * rows + n], y = src[(2 * kc + 1) * rows + n];
+        const float v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        uint4 *dst = out + b * per * parts + c;
+        uint32_t h[4], m[4], l[4];
+        if (parts == 3) {
+            split3_bf16x8(v, h, m, l);
+            dst[per] = make_uint4(m[0], m[1], m[2], m[3]);
+            dst[2 * per] = make_uint4(l[0], l[1], l[2], l[3]);
+        } else if (parts == 2) {
+            split_bf16x8(v, h, l);
+            dst[per] = make_uint4(l[0], l[1], l[2], l[3]);
+        } else {
+            round_bf16x8(v, h);
+        }
+        dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
     }
 }
 

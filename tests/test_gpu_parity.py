@@ -303,12 +303,16 @@ def test_full_size_n1m_r16_tensor_core_batch(bf):
     plan.destroy()
 
 
-def test_precision_ladder_tensor_core(bf):
-    """The tensor-core core's two rungs at N = 2^16, L = 12, r = 16, 128 RHS,
-    against the FP64 C oracle on sampled columns: 3xTF32 (the default) within
-    the FP32 tolerance; plain TF32 (one MMA per product, no low parts) at the
-    error TF32 operands give (relative ~1e-3: well above the FP32 bar, well
-    below 1)."""
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_precision_ladder_tensor_core(bf, adjoint):
+    """The tensor-core core's five rungs at N = 2^16, L = 12, r = 16, 128 RHS,
+    forward and adjoint, against the FP64 C oracle on sampled columns.  The
+    FP32-level rungs (3xTF32, the default, and the BF16 three-way split) are
+    within the FP32 tolerance.  The others sit where their operands' mantissas
+    put them, well above the FP32 bar and well below 1: plain TF32 (11 bits,
+    ~1e-3), the BF16 hi/lo split (16 bits, ~1e-5) and plain BF16 (8 bits,
+    ~6e-3).  The order of the rungs pins that each one really forms the
+    products it claims."""
     from bfinputs import complex_normal, synthetic_factors
     from oracle import capply
     from paper_1502_01379_gb300 import capi
@@ -316,14 +320,19 @@ def test_precision_ladder_tensor_core(bf):
     plan = bf.bf_plan_create(F, nrhs_max=128)
     g = complex_normal((128, F.N), seed=8, dtype=np.complex64)
     P = capply.PreparedFactors(F)
-    ref = [capply.bf_apply_c(P, g[j]) for j in (0, 77, 127)]
+    fn = capply.bf_adjoint_c if adjoint else capply.bf_apply_c
+    ref = [fn(P, g[j]) for j in (0, 77, 127)]
     errs = {}
-    for prec in (capi.BF_PREC_FP32, capi.BF_PREC_TF32):
+    for prec in (capi.BF_PREC_FP32, capi.BF_PREC_TF32, capi.BF_PREC_BF16X6, capi.BF_PREC_BF16X3, capi.BF_PREC_BF16):
         capi.bf_plan_set_precision(plan, prec)
-        u = _run(bf, plan, g)
+        u = _run(bf, plan, g, adjoint=adjoint)
         errs[prec] = max(_rel(u[j], r) for j, r in zip((0, 77, 127), ref))
     assert errs[capi.BF_PREC_FP32] < TOL
-    assert 1e-5 < errs[capi.BF_PREC_TF32] < 1e-2
+    assert errs[capi.BF_PREC_BF16X6] < TOL
+    assert 1e-4 < errs[capi.BF_PREC_TF32] < 1e-2
+    assert 2e-6 < errs[capi.BF_PREC_BF16X3] < 5e-5
+    assert 1e-3 < errs[capi.BF_PREC_BF16] < 3e-2
+    assert errs[capi.BF_PREC_BF16X6] < errs[capi.BF_PREC_BF16X3] < errs[capi.BF_PREC_TF32] < errs[capi.BF_PREC_BF16]
     with pytest.raises(capi.BfError):
         capi.bf_plan_set_precision(plan, 7)
     plan.destroy()
@@ -366,4 +375,32 @@ def test_workspace_allocation_failure_is_reported(bf):
     g = complex_normal((3, F.N), seed=6, dtype=np.complex64)
     plan = bf.bf_plan_create(F, nrhs_max=3)
     assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+    plan.destroy()
+
+
+def test_bf16_rungs_keep_split_blocks_only_while_set(bf):
+    """A BF16 rung splits the tensor-core blocks once into BF16 parts (2, 4
+    or 6 bytes per real entry beside the FP32 blocks' 4); switching back to
+    a TF32 rung releases them, and every switch reproduces the rung's result
+    bit for bit."""
+    from bfinputs import complex_normal, synthetic_factors
+    from paper_1502_01379_gb300 import capi
+    F = synthetic_factors(8, 16, 16, seed=12, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=64)
+    g = complex_normal((64, F.N), seed=13, dtype=np.complex64)
+    base = bf.bf_plan_device_bytes(plan)
+    out = {}
+    extra = {}
+    for prec in (capi.BF_PREC_BF16, capi.BF_PREC_BF16X3, capi.BF_PREC_BF16X6):
+        capi.bf_plan_set_precision(plan, prec)
+        extra[prec] = bf.bf_plan_device_bytes(plan) - base
+        out[prec] = _run(bf, plan, g)
+    assert extra[capi.BF_PREC_BF16] > 0
+    assert extra[capi.BF_PREC_BF16X3] == 2 * extra[capi.BF_PREC_BF16]
+    assert extra[capi.BF_PREC_BF16X6] == 3 * extra[capi.BF_PREC_BF16]
+    capi.bf_plan_set_precision(plan, capi.BF_PREC_FP32)
+    assert bf.bf_plan_device_bytes(plan) == base
+    for prec in (capi.BF_PREC_BF16X3, capi.BF_PREC_BF16):
+        capi.bf_plan_set_precision(plan, prec)
+        assert np.array_equal(_run(bf, plan, g), out[prec])
     plan.destroy()
