@@ -26,6 +26,12 @@ Modules (each function cites the passage of the paper it follows):
 * ``sparse``   -- an independent brute-force path: every factor assembled as
                   an explicit sparse matrix from the block-matrix displays of
                   Sec. 3, and the chain multiplied out.
+* ``quad``     -- the 2D carry-over on quadtrees (Sec. 1.2 notes it exists;
+                  the readings it takes are in its docstring): Morton order,
+                  a 2D FIO and the 2D DFT, construction with four children per
+                  node, apply and adjoint.
+* ``quad_sparse``-- the 2D factors assembled entry by entry as sparse
+                  matrices (independent of ``quad``'s reshapes).
 * ``capply``   -- ctypes binding of ``capply.c``: the same apply/adjoint as
                   plain C loops in FP64 (OpenMP over blocks), used for the
                   timed CPU baseline and for full-size parity.
