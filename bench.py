@@ -48,6 +48,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-operators line")
+    ap.add_argument("--no-quad", action="store_true", help="skip the 2D (quadtree) line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -331,7 +332,74 @@ def run_ours(args, rank, world, local):
         out["differentiation"] = diff_line(dev, stream)
     if not args.no_batch:
         out["batched"] = batch_line(dev, stream)
+    if not args.no_quad:
+        out["quad2d"] = quad_line(dev, stream)
     return out
+
+
+def fp32_fma_peak_tflops(dev) -> float:
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops x the maximum SM
+    clock (2070 MHz on GB300)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * 2.070e9 / 1e12
+
+
+def quad_line(dev, stream):
+    """The 2D workload: a 256 x 256 grid (N = 65536), quadtrees of depth 8 with
+    one point per leaf, rank 24 (level ranks 24, 24, 16, 4, 1), seeded
+    synthetic factor values; apply + adjoint of 1 and of 128 vectors through
+    the level kernels (FP32 on CUDA cores)."""
+    import numpy as np
+    import torch
+
+    from paper_1502_01379_gb300 import capi
+    from bfinputs import complex_normal
+    from bfinputs.quad import QUAD_CONFIGS, synthetic_quad_factors
+    cfg = QUAD_CONFIGS["fio2d_n65536_r24"]
+    F = synthetic_quad_factors(cfg["L"], cfg["n0"], cfg["r"], seed=0, dtype=np.complex64)
+    entries = F.nentries() - F.S.size            # complex entries of the dense group blocks (S folded in)
+    plan = capi.bf_quad_create(F, nrhs_max=cfg["nrhs"])
+    res = {"workload": "2D: butterfly factorization on quadtrees of a 2D-FIO-shaped N=65536 matrix (256x256 grid), "
+                       "L=8, leaf=1, r=24, seeded synthetic factor values; step = apply + adjoint",
+           "factor_entries": int(entries), "plan_device_gb": capi.bf_quad_device_bytes(plan) / 1e9,
+           "launches_per_apply": capi.bf_quad_passes(plan)}
+    peak, peak_src = load_peaks()
+    for nrhs in (1, cfg["nrhs"]):
+        g = torch.from_numpy(complex_normal((nrhs, F.N), seed=40 + nrhs, dtype=np.complex64)).to(dev)
+        u, v = torch.empty_like(g), torch.empty_like(g)
+
+        def step():
+            capi.bf_quad_apply(plan, g, u, stream=stream)
+            capi.bf_quad_apply(plan, u, v, adjoint=True, stream=stream)
+        reps = 20 if nrhs == 1 else 5
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ent = {"vectors_per_s": 2 * nrhs / (ms / 1e3), "ms_per_apply": ms / 2}
+        if nrhs == 1:
+            alg = entries * 8 + 2 * F.N * 8
+            ent["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 2 / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                               "frac": alg / (ms / 2 / 1e3) / 1e9 / peak, "peak_source": peak_src,
+                               "bytes_note": "per apply: every dense group block once (complex64) + in/out vectors"}
+        else:
+            flops = 8.0 * entries * nrhs
+            fp = fp32_fma_peak_tflops(dev)
+            ent["roofline"] = {"bound": "fma", "achieved": flops / (ms / 2 / 1e3) / 1e12, "peak": fp,
+                               "unit": "TFLOP/s", "frac": flops / (ms / 2 / 1e3) / 1e12 / fp,
+                               "peak_source": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                               "flops_note": "8 real flops per complex multiply-add of every dense group block"}
+        res[f"nrhs_{nrhs}"] = ent
+        del g, u, v
+    plan.destroy()
+    return res
 
 
 def batch_line(dev, stream):

@@ -305,6 +305,53 @@ typedef enum {
 } bf_precision;
 bf_status bf_plan_set_precision(bf_plan plan, int precision);
 
+/* ---------------------------------------------------------------------------
+ * 2D factorizations on quadtrees.  The paper develops the factorization in
+ * 1D and notes that it carries over to higher dimensions (Sec. 1.2); this is
+ * that carry-over for an n x n grid, N = n^2: quadtrees of even depth L, four
+ * children per node, n0 = N / 4^L points per leaf, h = L/2, m = 4^h.  Points
+ * and frequencies are numbered in quadtree (Morton) order, so a node's points
+ * are contiguous and child c holds its c-th quarter.  Level l uses rank
+ * r_l = min(r, N / 4^l) (l = h..L).  The factors use bf_factors with these
+ * shapes (row-major, block index first; nb = 4^L):
+ *   VL      nb blocks of n0 x r_L: block b is V^L_{b,0}.
+ *   H[t]    level l = h + t: nb blocks of r_{l+1} x 4 r_l; block
+ *           j''*4^{L-l-1} + i' is H^l_{j'',i'} (column node j'' at level l+1,
+ *           row node i' at level L-l-1).
+ *   S       m*m*r_h reals: S[(i*m + j)*r_h + k] is entry k of S^h_{i,j}.
+ *   G[t]    as H: block i''*4^{L-l-1} + j' is G^l_{i'',j'}.
+ *   UL      nb blocks of n0 x r_L: block a is U^L_{a,0}.
+ * The plan multiplies out, in FP64, one dense (4 r_out) x (4 r_in) block per
+ * group of four vectors a level acts on (the leaf factors folded into the
+ * first and last level, S^h into the first splitting level), stores them in
+ * complex64 and applies them level by level on CUDA cores in FP32.
+ * ------------------------------------------------------------------------- */
+typedef struct bf_quad_s *bf_quad;
+
+/* Builds a 2D plan from desc (L even, 2 <= L <= 12; leaf a power of 4 up to
+ * 16; 1 <= r <= 32; nrhs_max >= 1) and host factors.  Holds both directions'
+ * blocks (complex64) and two workspaces of 4^L r_h nrhs_max entries.
+ * Synchronizes `stream`.  BF_ERR_INVALID for a bad shape or NULL array,
+ * BF_ERR_UNSUPPORTED outside the limits, BF_ERR_NOMEM if memory runs out;
+ * on error *plan is NULL. */
+bf_status bf_quad_create(bf_quad *plan, const bf_desc *desc, const bf_factors *factors, cudaStream_t stream);
+
+/* out = K_bf in (adjoint = 0) or K_bf^* in, for nrhs vectors: DEVICE
+ * pointers to column-major N x nrhs complex64 arrays with leading dimension
+ * ld >= N, in Morton point order; in and out must not overlap
+ * (BF_ERR_INVALID, as are host pointers).  Runs in chunks of nrhs_max
+ * vectors, L launches each.  Asynchronous on `stream`; calls on one plan
+ * must not overlap (one workspace). */
+bf_status bf_quad_apply(bf_quad plan, const void *in, void *out, int nrhs, long long ld, int adjoint,
+                        cudaStream_t stream);
+
+/* Device bytes held (blocks of both directions and workspaces), kernel
+ * launches per chunk and direction (L), and release (synchronizes the device;
+ * NULL accepted). */
+size_t bf_quad_device_bytes(bf_quad plan);
+int bf_quad_passes(bf_quad plan);
+bf_status bf_quad_destroy(bf_quad plan);
+
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);
 

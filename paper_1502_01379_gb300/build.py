@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libbfly.so")
-SOURCES = [os.path.join(CSRC, "bf_capi.cu"), os.path.join(CSRC, "bf_diff.cu")]
+SOURCES = [os.path.join(CSRC, "bf_capi.cu"), os.path.join(CSRC, "bf_diff.cu"), os.path.join(CSRC, "bf_quad.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, n) for n in sorted(os.listdir(CSRC)) if n.endswith(".cuh")] + [
     os.path.join(INCLUDE, "bfly.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,22 +36,31 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in DEPS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library if it is missing or older than its sources; return its path."""
-    if not force and not stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", CSRC, *SOURCES, "-o", tmp]
+def _run(cmd: list, verbose: bool) -> None:
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
     if verbose:
         print(res.stdout + res.stderr)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the library if it is missing or older than its sources; return
+    its path.  The translation units compile in parallel, then link."""
+    if not force and not stale():
+        return LIB
+    from concurrent.futures import ThreadPoolExecutor
+    os.makedirs(OUT_DIR, exist_ok=True)
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if verbose:
+        flags.insert(0, "-Xptxas=-v")
+    objs = [os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o") for src in SOURCES]
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        list(ex.map(lambda so: _run([nvcc(), *flags, "-c", so[0], "-o", so[1]], verbose), zip(SOURCES, objs)))
+    tmp = LIB + ".tmp"
+    _run([nvcc(), "-shared", *ARCH, *objs, "-o", tmp], verbose)
     os.replace(tmp, LIB)
     return LIB
 

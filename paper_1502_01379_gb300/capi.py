@@ -23,7 +23,8 @@ EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", 
            "bf_plan_device_bytes", "bf_plan_set_profiling", "bf_plan_kernel_times", "bf_status_string",
            "bf_apply_static_scratch", "bf_diff_create", "bf_diff_destroy", "bf_diff_stride",
            "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
-           "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision")
+           "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision", "bf_quad_create",
+           "bf_quad_apply", "bf_quad_device_bytes", "bf_quad_passes", "bf_quad_destroy")
 BF_PREC_FP32, BF_PREC_TF32, BF_PREC_BF16X3, BF_PREC_BF16, BF_PREC_BF16X6 = 0, 1, 2, 3, 4
 BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
@@ -97,6 +98,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "bf_batch_check": (i, [vp, vp]),
         "bf_batch_items": (i, [vp]),
         "bf_batch_destroy": (i, [vp]),
+        "bf_quad_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_desc), ctypes.POINTER(bf_factors), vp]),
+        "bf_quad_apply": (i, [vp, vp, vp, i, ll, i, vp]),
+        "bf_quad_device_bytes": (ctypes.c_size_t, [vp]),
+        "bf_quad_passes": (i, [vp]),
+        "bf_quad_destroy": (i, [vp]),
         "bf_diff_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_diff_desc)]),
         "bf_diff_destroy": (i, [vp]),
         "bf_diff_stride": (i, [vp]),
@@ -213,6 +219,57 @@ def bf_apply_adjoint(plan: Plan, x, y, nrhs: int | None = None, ld: int | None =
     xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
     _check(load().bf_apply_adjoint(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi), n, l,
                                    ctypes.c_void_p(_stream_handle(stream))), "bf_apply_adjoint")
+
+
+class QuadPlan:
+    """Owns a bf_quad handle (2D factorization on quadtrees)."""
+
+    def __init__(self, handle: int, N: int, L: int, n0: int, r: int, nrhs_max: int):
+        self.handle, self.N, self.L, self.n0, self.r, self.nrhs_max = handle, N, L, n0, r, nrhs_max
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self) -> None:
+        if getattr(self, "handle", None):
+            load().bf_quad_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def bf_quad_create(factors, nrhs_max: int = 1, stream=None) -> QuadPlan:
+    """Create a 2D plan from quadtree factors in canonical layout (an object
+    with L, n0, r, VL, H, S, G, UL; complex64 or complex128)."""
+    f, keep = _host_factors(factors)
+    d = bf_desc(int(factors.L), int(factors.n0), int(factors.r), int(nrhs_max))
+    h = ctypes.c_void_p()
+    _check(load().bf_quad_create(ctypes.byref(h), ctypes.byref(d), ctypes.byref(f),
+                                 ctypes.c_void_p(_stream_handle(stream))), "bf_quad_create")
+    del keep
+    return QuadPlan(h.value, int(factors.n0) << (2 * int(factors.L)), int(factors.L), int(factors.n0),
+                    int(factors.r), int(nrhs_max))
+
+
+def bf_quad_apply(plan: QuadPlan, x, y, nrhs: int | None = None, ld: int | None = None, adjoint: bool = False,
+                  stream=None) -> None:
+    """y = K_bf x (or K_bf^* x) for a 2D plan; device tensors (asynchronous)."""
+    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
+    _check(load().bf_quad_apply(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi), n, l,
+                                1 if adjoint else 0, ctypes.c_void_p(_stream_handle(stream))), "bf_quad_apply")
+
+
+def bf_quad_device_bytes(plan: QuadPlan) -> int:
+    return int(load().bf_quad_device_bytes(ctypes.c_void_p(plan.handle)))
+
+
+def bf_quad_passes(plan: QuadPlan) -> int:
+    return int(load().bf_quad_passes(ctypes.c_void_p(plan.handle)))
+
+
+def bf_quad_destroy(plan: QuadPlan) -> None:
+    plan.destroy()
 
 
 def bf_plan_set_precision(plan: Plan, precision: int) -> None:

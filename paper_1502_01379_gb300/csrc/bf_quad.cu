@@ -1,0 +1,386 @@
+// 2D (quadtree) butterfly factorizations: plan and apply, sm_103a.
+//
+// The 2D factorization has the 1D form K ~ U^L G^{L-1} ... G^h M^h
+// (H^h)^* ... (H^{L-1})^* (V^L)^* with four children per tree node (the
+// extension to higher dimensions that Sec. 1.2 points to).  Level l carries,
+// for every pair (node of one tree at level l, node of the other at level
+// L-l), a vector of r_l = min(r, N/4^l) entries.  One transfer level acts on
+// closed groups of four such vectors:
+//   splitting (G^l):  [w_{i,4j'} .. w_{i,4j'+3}] -> w_{4i+c,j'} = G^l_{4i+c,j'} [..],
+//   merging ((H^l)^*): t_{4j+c,i'} (c = 0..3) -> [t_{j,4i'} .. t_{j,4i'+3}] = sum_c (H^l_{4j+c,i'})^* t_{4j+c,i'},
+// i.e. per group one dense complex block of (4 r_out) x (4 r_in).  The plan
+// forms these blocks in FP64 when it is created -- the leaf factor folded
+// into the first and last pass, the real diagonal S^h of M^h into the first
+// splitting pass -- so the apply is L passes of the same operation:
+//     out_stack(group) = F(group) in_stack(group),
+// where the four input (output) blocks of group (A, B) sit at block indices
+// a A + b B + c s (c = 0..3) of the level's vector, with block size r_in
+// (r_out) or n0 at the leaves.  The vectors at level l are ordered (node of
+// the first tree, node of the second), so a group's four blocks are either
+// consecutive or 4^{L-l-1} apart; the first splitting pass reads the merging
+// half's output transposed (M^h).
+//
+// Kernel: one thread block per (group, tile of NT right-hand sides); the
+// input stack (Kin x NT) is staged in shared memory; thread o accumulates
+// output o of the stack for the NT vectors in FP32 while it streams column o
+// of F (stored k-major, F^T, so a warp's loads of one k are contiguous).  One
+// vector at a time this is a stream over the factors (HBM-bound); with NT = 32
+// every factor entry feeds 32 complex multiply-adds.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/bfly.h"
+
+namespace bfq {
+
+constexpr int kMaxL = 12;
+constexpr int kMaxStack = 128;   // Kin, Nout per group (4 r_l, 4 n0)
+
+struct Pass {
+    const float2 *F;             // per group: Kin x Nout complex, k-major (F^T)
+    int nA, nB;                  // groups (A, B): A < nA, B < nB
+    long long ain, bin, sin;     // block index of input child c: ain A + bin B + c sin
+    long long aout, bout, sout;
+    int bsz_in, bsz_out;         // entries per block
+    int Kin, Nout;               // 4 bsz_in, 4 bsz_out
+};
+
+template <int NT>
+__global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const float2 *__restrict__ in, long long ld_in,
+                                                        float2 *__restrict__ out, long long ld_out, int nrhs) {
+    extern __shared__ float2 xs[];   // [Kin][NT]
+    const int ntiles = (nrhs + NT - 1) / NT;
+    const long long g = blockIdx.x / ntiles;
+    const int tile = (int)(blockIdx.x - g * ntiles);
+    const int A = (int)(g / p.nB), B = (int)(g - (long long)A * p.nB);
+    const int rhs0 = tile * NT, nt = min(NT, nrhs - rhs0);
+    const long long in_base = p.ain * A + p.bin * B;
+    for (int idx = threadIdx.x; idx < p.Kin * NT; idx += blockDim.x) {
+        const int j = idx / p.Kin, k = idx - j * p.Kin;
+        const int c = k / p.bsz_in, x = k - c * p.bsz_in;
+        const long long pos = (in_base + c * p.sin) * p.bsz_in + x;
+        xs[k * NT + j] = j < nt ? in[(long long)(rhs0 + j) * ld_in + pos] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const long long out_base = p.aout * A + p.bout * B;
+    const float2 *Fg = p.F + g * (long long)p.Kin * p.Nout;
+    for (int o = threadIdx.x; o < p.Nout; o += blockDim.x) {
+        float2 acc[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[j] = make_float2(0.f, 0.f);
+        const float2 *f = Fg + o;
+#pragma unroll 4
+        for (int k = 0; k < p.Kin; ++k) {
+            const float2 fv = __ldg(f + (long long)k * p.Nout);
+            const float2 *xk = xs + k * NT;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const float2 xv = xk[j];
+                acc[j].x = fmaf(fv.x, xv.x, fmaf(-fv.y, xv.y, acc[j].x));
+                acc[j].y = fmaf(fv.x, xv.y, fmaf(fv.y, xv.x, acc[j].y));
+            }
+        }
+        const int c = o / p.bsz_out, x = o - c * p.bsz_out;
+        const long long pos = (out_base + c * p.sout) * p.bsz_out + x;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+            if (j < nt) out[(long long)(rhs0 + j) * ld_out + pos] = acc[j];
+    }
+}
+
+struct HostPass {
+    Pass p;
+    float2 *d = nullptr;
+};
+
+}  // namespace
+
+struct bf_quad_s {
+    int L = 0, n0 = 0, r = 0, h = 0, nrhs_max = 0;
+    long long N = 0, m = 0, Rmax = 0;
+    int ranks[bfq::kMaxL + 1] = {};
+    std::vector<bfq::HostPass> fwd, adj;
+    float2 *ws[2] = {nullptr, nullptr};
+    size_t device_bytes = 0;
+    int num_sms = 1;
+};
+
+namespace {
+
+using cd = std::complex<double>;
+
+bf_status qfail(cudaError_t) {
+    cudaGetLastError();
+    return BF_ERR_CUDA;
+}
+
+// Factor entry readers over the caller's host arrays (complex64 or complex128).
+struct Reader {
+    int dtype;
+    cd at(const void *base, long long idx) const {
+        if (dtype == BF_C128) {
+            const double *p = static_cast<const double *>(base) + 2 * idx;
+            return cd(p[0], p[1]);
+        }
+        const float *p = static_cast<const float *>(base) + 2 * idx;
+        return cd(p[0], p[1]);
+    }
+    double real(const void *base, long long idx) const {
+        return dtype == BF_C128 ? static_cast<const double *>(base)[idx] : (double)static_cast<const float *>(base)[idx];
+    }
+};
+
+long long pow4(int e) { return 1LL << (2 * e); }
+
+// Runs fn(g) for g in [0, n) on the host's cores.
+template <class Fn>
+void parallel_for(long long n, Fn fn) {
+    const int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&, t] {
+            for (long long g = n * t / nt; g < n * (t + 1) / nt; ++g) fn(g);
+        });
+    for (auto &th : pool) th.join();
+}
+
+// The passes of one direction.  Forward: merging with (H, V^L), splitting with
+// (G, U^L), S[i][j]; adjoint: merging with (G, U^L), splitting with (H, V^L),
+// S transposed (K^* = V^L H ... (M^h)^* (G^h)^* ... (U^L)^*).
+bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::vector<bfq::HostPass> &out) {
+    const Reader rd{f.dtype};
+    const int L = Q.L, h = Q.h, n0 = Q.n0;
+    const int *rk = Q.ranks;
+    const void *const *Dn = adjoint ? f.G : f.H;     // merging transfer blocks
+    const void *leafDn = adjoint ? f.UL : f.VL;
+    const void *const *Up = adjoint ? f.H : f.G;     // splitting transfer blocks
+    const void *leafUp = adjoint ? f.VL : f.UL;
+    const long long m = Q.m;
+    for (int half = 0; half < 2; ++half) {
+        for (int s = 0; s < L - h; ++s) {
+            const int lv = half == 0 ? L - 1 - s : h + s;
+            const long long nA = pow4(lv), nB = pow4(L - lv - 1);
+            bfq::Pass p{};
+            p.nA = (int)nA;
+            p.nB = (int)nB;
+            const int r0 = rk[lv], r1 = rk[lv + 1];
+            const bool leaf = lv == L - 1;
+            if (half == 0) {   // merging: in blocks (4A + c) nB + B, out A 4nB + 4B + c
+                p.ain = 4 * nB, p.bin = 1, p.sin = nB;
+                p.aout = 4 * nB, p.bout = 4, p.sout = 1;
+                p.bsz_in = leaf ? n0 : r1;
+                p.bsz_out = r0;
+            } else {           // splitting: in A 4nB + 4B + c (or M^h's transpose), out (4A + c) nB + B
+                if (lv == h) p.ain = 1, p.bin = 4 * m, p.sin = m;
+                else p.ain = 4 * nB, p.bin = 4, p.sin = 1;
+                p.aout = 4 * nB, p.bout = 1, p.sout = nB;
+                p.bsz_in = r0;
+                p.bsz_out = leaf ? n0 : r1;
+            }
+            p.Kin = 4 * p.bsz_in;
+            p.Nout = 4 * p.bsz_out;
+            if (p.Kin > bfq::kMaxStack || p.Nout > bfq::kMaxStack) return BF_ERR_UNSUPPORTED;
+            const long long ngroups = nA * nB;
+            const size_t per = (size_t)p.Kin * p.Nout;
+            std::vector<float2> host;
+            try {
+                host.resize(per * ngroups);
+            } catch (const std::bad_alloc &) {
+                return BF_ERR_NOMEM;
+            }
+            const void *T = half == 0 ? Dn[lv - h] : Up[lv - h];
+            parallel_for(ngroups, [&](long long g) {
+                const long long A = g / nB, B = g - A * nB;
+                float2 *Fg = host.data() + per * g;   // Fg[k * Nout + o]
+                std::vector<cd> blk((size_t)p.Kin * p.Nout);   // blk[o * Kin + k]
+                for (int c = 0; c < 4; ++c) {
+                    const long long b = (4 * A + c) * nB + B;   // transfer block index of child c
+                    const long long tb = b * r1 * 4 * r0;       // its first entry (r1 x 4 r0, row-major)
+                    if (half == 0) {
+                        // column block c: (T_b)^* (4 r0 x r1), times (leaf_{4A+c})^* (r_L x n0) at the leaves
+                        for (int o = 0; o < 4 * r0; ++o)
+                            for (int k = 0; k < p.bsz_in; ++k) {
+                                cd v;
+                                if (!leaf) {
+                                    v = std::conj(rd.at(T, tb + (long long)k * 4 * r0 + o));
+                                } else {
+                                    for (int a = 0; a < r1; ++a)
+                                        v += std::conj(rd.at(T, tb + (long long)a * 4 * r0 + o)) *
+                                             std::conj(rd.at(leafDn, (b * n0 + k) * r1 + a));
+                                }
+                                blk[(size_t)o * p.Kin + c * p.bsz_in + k] = v;
+                            }
+                    } else {
+                        // row block c: T_b (r1 x 4 r0), times leaf_{4A+c} (n0 x r_L) on the left at the leaves
+                        for (int o = 0; o < p.bsz_out; ++o)
+                            for (int k = 0; k < 4 * r0; ++k) {
+                                cd v;
+                                if (!leaf) {
+                                    v = rd.at(T, tb + (long long)o * 4 * r0 + k);
+                                } else {
+                                    for (int a = 0; a < r1; ++a)
+                                        v += rd.at(leafUp, (b * n0 + o) * r1 + a) * rd.at(T, tb + (long long)a * 4 * r0 + k);
+                                }
+                                if (lv == h) {   // M^h: column c' r_h + x carries S of block (row node, column node)
+                                    const int cp = k / r0, x = k - cp * r0;
+                                    const long long i = adjoint ? 4 * B + cp : A, j = adjoint ? A : 4 * B + cp;
+                                    v *= rd.real(f.S, (i * m + j) * r0 + x);
+                                }
+                                blk[(size_t)(c * p.bsz_out + o) * p.Kin + k] = v;
+                            }
+                    }
+                }
+                for (int o = 0; o < p.Nout; ++o)
+                    for (int k = 0; k < p.Kin; ++k) {
+                        const cd v = blk[(size_t)o * p.Kin + k];
+                        Fg[(size_t)k * p.Nout + o] = make_float2((float)v.real(), (float)v.imag());
+                    }
+            });
+            bfq::HostPass hp;
+            hp.p = p;
+            if (cudaMalloc(&hp.d, host.size() * sizeof(float2)) != cudaSuccess) {
+                cudaGetLastError();
+                return BF_ERR_NOMEM;
+            }
+            out.push_back(hp);
+            Q.device_bytes += host.size() * sizeof(float2);
+            if (cudaMemcpy(hp.d, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+                return qfail(cudaErrorUnknown);
+            out.back().p.F = hp.d;
+        }
+    }
+    return BF_OK;
+}
+
+void free_quad(bf_quad_s *Q) {
+    if (!Q) return;
+    for (auto *d : {&Q->fwd, &Q->adj})
+        for (auto &hp : *d) cudaFree(hp.d);
+    cudaFree(Q->ws[0]);
+    cudaFree(Q->ws[1]);
+    delete Q;
+}
+
+template <int NT>
+cudaError_t launch_pass(const bfq::Pass &p, const float2 *in, long long ld_in, float2 *out, long long ld_out, int nrhs,
+                        cudaStream_t s) {
+    const long long ntiles = (nrhs + NT - 1) / NT;
+    const long long blocks = (long long)p.nA * p.nB * ntiles;
+    const int threads = std::min(128, (p.Nout + 31) / 32 * 32);
+    const size_t smem = (size_t)p.Kin * NT * sizeof(float2);
+    bfq::quad_pass_kernel<NT><<<(unsigned)blocks, threads, smem, s>>>(p, in, ld_in, out, ld_out, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t run_pass(const bfq::Pass &p, const float2 *in, long long ld_in, float2 *out, long long ld_out, int nrhs,
+                     cudaStream_t s) {
+    if (nrhs >= 32) return launch_pass<32>(p, in, ld_in, out, ld_out, nrhs, s);
+    if (nrhs >= 16) return launch_pass<16>(p, in, ld_in, out, ld_out, nrhs, s);
+    if (nrhs >= 8) return launch_pass<8>(p, in, ld_in, out, ld_out, nrhs, s);
+    if (nrhs >= 4) return launch_pass<4>(p, in, ld_in, out, ld_out, nrhs, s);
+    if (nrhs >= 2) return launch_pass<2>(p, in, ld_in, out, ld_out, nrhs, s);
+    return launch_pass<1>(p, in, ld_in, out, ld_out, nrhs, s);
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f, cudaStream_t stream) {
+    if (!out) return BF_ERR_INVALID;
+    *out = nullptr;
+    if (!desc || !f || !f->VL || !f->UL || !f->S || !f->H || !f->G) return BF_ERR_INVALID;
+    if (f->dtype != BF_C64 && f->dtype != BF_C128) return BF_ERR_INVALID;
+    const int L = desc->L, n0 = desc->leaf, r = desc->r;
+    if (L < 2 || L % 2 || desc->nrhs_max < 1 || r < 1 || n0 < 1) return BF_ERR_INVALID;
+    if ((n0 & (n0 - 1)) || (n0 & 0xAAAAAAAA)) return BF_ERR_INVALID;   // a power of 4
+    if (L > bfq::kMaxL || r > 32 || n0 > 16) return BF_ERR_UNSUPPORTED;
+    for (int t = 0; t < L / 2; ++t)
+        if (!f->H[t] || !f->G[t]) return BF_ERR_INVALID;
+    bf_quad_s *Q = new (std::nothrow) bf_quad_s;
+    if (!Q) return BF_ERR_NOMEM;
+    Q->L = L;
+    Q->n0 = n0;
+    Q->r = r;
+    Q->h = L / 2;
+    Q->nrhs_max = desc->nrhs_max;
+    Q->N = (long long)n0 << (2 * L);
+    Q->m = pow4(Q->h);
+    for (int lv = Q->h; lv <= L; ++lv) Q->ranks[lv] = (int)std::min<long long>(r, Q->N >> (2 * lv));
+    Q->Rmax = pow4(L) * Q->ranks[Q->h];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&Q->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    bf_status st = build_direction(*Q, *f, false, Q->fwd);
+    if (st == BF_OK) st = build_direction(*Q, *f, true, Q->adj);
+    if (st == BF_OK) {
+        const size_t ws = (size_t)Q->Rmax * Q->nrhs_max * sizeof(float2);
+        for (auto &w : Q->ws)
+            if (st == BF_OK && cudaMalloc(&w, ws) != cudaSuccess) {
+                cudaGetLastError();
+                w = nullptr;
+                st = BF_ERR_NOMEM;
+            }
+        if (st == BF_OK) Q->device_bytes += 2 * ws;
+    }
+    if (st == BF_OK && cudaStreamSynchronize(stream) != cudaSuccess) st = qfail(cudaErrorUnknown);
+    if (st != BF_OK) {
+        free_quad(Q);
+        return st;
+    }
+    *out = Q;
+    return BF_OK;
+}
+
+bf_status bf_quad_apply(bf_quad Q, const void *in, void *out, int nrhs, long long ld, int adjoint,
+                        cudaStream_t stream) {
+    if (!Q || nrhs < 0) return BF_ERR_INVALID;
+    if (nrhs == 0) return BF_OK;
+    if (!in || !out || ld < Q->N) return BF_ERR_INVALID;
+    const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+    const long long span = ((long long)(nrhs - 1) * ld + Q->N) * 8;
+    if (a < b + span && b < a + span) return BF_ERR_INVALID;
+    if (!is_device_ptr(in) || !is_device_ptr(out)) return BF_ERR_INVALID;
+    const auto &D = adjoint ? Q->adj : Q->fwd;
+    const int np = (int)D.size();
+    for (int k0 = 0; k0 < nrhs; k0 += Q->nrhs_max) {
+        const int nc = std::min(Q->nrhs_max, nrhs - k0);
+        const float2 *src = static_cast<const float2 *>(in) + (long long)k0 * ld;
+        float2 *dst = static_cast<float2 *>(out) + (long long)k0 * ld;
+        for (int ps = 0; ps < np; ++ps) {
+            const float2 *pin = ps == 0 ? src : Q->ws[(ps - 1) & 1];
+            float2 *pout = ps == np - 1 ? dst : Q->ws[ps & 1];
+            const long long lin = ps == 0 ? ld : Q->Rmax, lout = ps == np - 1 ? ld : Q->Rmax;
+            if (run_pass(D[ps].p, pin, lin, pout, lout, nc, stream) != cudaSuccess) return qfail(cudaErrorUnknown);
+        }
+    }
+    return BF_OK;
+}
+
+size_t bf_quad_device_bytes(bf_quad Q) { return Q ? Q->device_bytes : 0; }
+
+int bf_quad_passes(bf_quad Q) { return Q ? (int)Q->fwd.size() : 0; }
+
+bf_status bf_quad_destroy(bf_quad Q) {
+    if (!Q) return BF_OK;
+    cudaDeviceSynchronize();
+    free_quad(Q);
+    return BF_OK;
+}
+
+}  // extern "C"
