@@ -346,11 +346,26 @@ bf_status bf_quad_apply(bf_quad plan, const void *in, void *out, int nrhs, long 
                         cudaStream_t stream);
 
 /* Device bytes held (blocks of both directions and workspaces), kernel
- * launches per chunk and direction (L), and release (synchronizes the device;
- * NULL accepted). */
+ * launches per chunk and direction (L), how many of them run on the tensor
+ * cores for chunks of 32 or more vectors, and release (synchronizes the
+ * device; NULL accepted). */
 size_t bf_quad_device_bytes(bf_quad plan);
 int bf_quad_passes(bf_quad plan);
+int bf_quad_tc_passes(bf_quad plan);
 bf_status bf_quad_destroy(bf_quad plan);
+
+/* Tensor-core path of a 2D plan.  When nrhs_max >= 32 the plan also keeps
+ * every level except the two that read and write the caller's vectors in
+ * the tensor-core core's form (a group's stack split into output parts and
+ * K-chunks of at most 64 that are multiples of 16, each a [Re F; Im F]
+ * block; the K-chunks accumulate in tensor memory), and chunks of 32 or more
+ * vectors run those levels on the tensor cores, with 128-vector planar tiles
+ * between all levels.  bf_quad_set_precision picks the rung exactly as
+ * bf_plan_set_precision does (BF16 rungs split the blocks once, synchronously);
+ * bf_quad_check reads and clears the error word of the tensor-core kernel's
+ * bounded waits (BF_ERR_TIMEOUT), synchronizing `stream`. */
+bf_status bf_quad_set_precision(bf_quad plan, int precision);
+bf_status bf_quad_check(bf_quad plan, cudaStream_t stream);
 
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);

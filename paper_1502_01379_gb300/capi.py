@@ -24,7 +24,8 @@ EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", 
            "bf_apply_static_scratch", "bf_diff_create", "bf_diff_destroy", "bf_diff_stride",
            "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
            "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision", "bf_quad_create",
-           "bf_quad_apply", "bf_quad_device_bytes", "bf_quad_passes", "bf_quad_destroy")
+           "bf_quad_apply", "bf_quad_device_bytes", "bf_quad_passes", "bf_quad_destroy", "bf_quad_tc_passes",
+           "bf_quad_set_precision", "bf_quad_check")
 BF_PREC_FP32, BF_PREC_TF32, BF_PREC_BF16X3, BF_PREC_BF16, BF_PREC_BF16X6 = 0, 1, 2, 3, 4
 BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
@@ -103,6 +104,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "bf_quad_device_bytes": (ctypes.c_size_t, [vp]),
         "bf_quad_passes": (i, [vp]),
         "bf_quad_destroy": (i, [vp]),
+        "bf_quad_tc_passes": (i, [vp]),
+        "bf_quad_set_precision": (i, [vp, i]),
+        "bf_quad_check": (i, [vp, vp]),
         "bf_diff_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_diff_desc)]),
         "bf_diff_destroy": (i, [vp]),
         "bf_diff_stride": (i, [vp]),
@@ -266,6 +270,21 @@ def bf_quad_device_bytes(plan: QuadPlan) -> int:
 
 def bf_quad_passes(plan: QuadPlan) -> int:
     return int(load().bf_quad_passes(ctypes.c_void_p(plan.handle)))
+
+
+def bf_quad_tc_passes(plan: QuadPlan) -> int:
+    return int(load().bf_quad_tc_passes(ctypes.c_void_p(plan.handle)))
+
+
+def bf_quad_set_precision(plan: QuadPlan, precision: int) -> None:
+    """Operand precision of a 2D plan's tensor-core levels (the rungs of bf_plan_set_precision)."""
+    _check(load().bf_quad_set_precision(ctypes.c_void_p(plan.handle), int(precision)), "bf_quad_set_precision")
+
+
+def bf_quad_check(plan: QuadPlan, stream=None) -> None:
+    """Raises BfError(BF_ERR_TIMEOUT) if a tensor-core wait expired since the last check."""
+    _check(load().bf_quad_check(ctypes.c_void_p(plan.handle), ctypes.c_void_p(_stream_handle(stream))),
+           "bf_quad_check")
 
 
 def bf_quad_destroy(plan: QuadPlan) -> None:

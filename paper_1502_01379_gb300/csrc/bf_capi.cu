@@ -5,6 +5,7 @@
 #include "bf_kernels.cuh"
 #include "bf_wide.cuh"
 #include "bf_tc.cuh"
+#include "bf_internal.h"
 
 #include <algorithm>
 #include <complex>
@@ -1468,3 +1469,58 @@ bf_status bf_batch_destroy(bf_batch B) {
 }
 
 }  // extern "C"
+
+namespace bfint {
+
+cudaError_t tc_prepare() {
+    return cudaFuncSetAttribute(bftc::bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bftc::kSmemBytes);
+}
+
+cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
+    bftc::TcParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.fac = q.fac;
+    p.fac16 = q.fac16;
+    p.in = q.in;
+    p.out = q.out;
+    p.R = q.R;
+    p.err = q.err;
+    p.load_kind = bftc::LD_QUAD;
+    p.store_kind = bftc::ST_QUAD;
+    p.m = 1;
+    p.ngroups = 1;
+    p.Kin = q.Kin;
+    p.Nout = q.Nout;
+    p.nrhs = q.nrhs;
+    p.split = q.split;
+    p.bf16 = q.bf16;
+    p.q_ain = q.ain;
+    p.q_bin = q.bin;
+    p.q_sin = q.sin;
+    p.q_aout = q.aout;
+    p.q_bout = q.bout;
+    p.q_sout = q.sout;
+    p.q_bszi = q.bszi;
+    p.q_bszo = q.bszo;
+    p.q_nB = q.nB;
+    p.q_ngroups = q.ngroups;
+    p.q_parts = q.parts;
+    p.q_chunks = q.chunks;
+    const long long ntiles = (q.nrhs + bftc::NR - 1) / bftc::NR;
+    const long long items = (long long)q.ngroups * q.parts * ntiles;
+    const int grid = (int)std::min<long long>(items, num_sms);
+    bftc::bf_tc_kernel<<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t bf16_split(const float *fac, uint16_t *out, long long nblocks, int rows, int Kin, int parts,
+                       int num_sms) {
+    const long long chunks = nblocks * rows * Kin / 8;
+    const int grid = (int)std::min<long long>((chunks + 255) / 256, 8LL * num_sms);
+    bftc::bf16_split_kernel<<<grid, 256>>>(fac, reinterpret_cast<uint4 *>(out), nblocks, rows, Kin, parts);
+    return cudaGetLastError();
+}
+
+int tc_boff(int n, int k, int rows) { return bftc::boff(n, k, rows); }
+
+}  // namespace bfint

@@ -30,12 +30,14 @@
 
 #include <algorithm>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <thread>
 #include <vector>
 
 #include "../../include/bfly.h"
+#include "bf_internal.h"
 
 namespace bfq {
 
@@ -49,7 +51,15 @@ struct Pass {
     long long aout, bout, sout;
     int bsz_in, bsz_out;         // entries per block
     int Kin, Nout;               // 4 bsz_in, 4 bsz_out
+    int in_planar, out_planar;   // vectors as planar 128-RHS tiles of R positions (else RHS-major with ld)
+    long long R;
 };
+
+// Address of (vector j, position pos) in a planar tile buffer: tile j / 128
+// holds, per position, the 128 real parts then the 128 imaginary parts.
+__device__ __forceinline__ long long planar_at(long long R, long long j, long long pos) {
+    return ((j >> 7) * R + pos) * 256 + (j & 127);
+}
 
 template <int NT>
 __global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const float2 *__restrict__ in, long long ld_in,
@@ -62,10 +72,21 @@ __global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const floa
     const int rhs0 = tile * NT, nt = min(NT, nrhs - rhs0);
     const long long in_base = p.ain * A + p.bin * B;
     for (int idx = threadIdx.x; idx < p.Kin * NT; idx += blockDim.x) {
-        const int j = idx / p.Kin, k = idx - j * p.Kin;
+        // consecutive threads: consecutive positions of one vector (RHS-major) or
+        // consecutive vectors at one position (planar)
+        const int j = p.in_planar ? idx % NT : idx / p.Kin, k = p.in_planar ? idx / NT : idx - j * p.Kin;
         const int c = k / p.bsz_in, x = k - c * p.bsz_in;
         const long long pos = (in_base + c * p.sin) * p.bsz_in + x;
-        xs[k * NT + j] = j < nt ? in[(long long)(rhs0 + j) * ld_in + pos] : make_float2(0.f, 0.f);
+        float2 v = make_float2(0.f, 0.f);
+        if (j < nt) {
+            if (p.in_planar) {
+                const float *f = reinterpret_cast<const float *>(in) + planar_at(p.R, rhs0 + j, pos);
+                v = make_float2(f[0], f[128]);
+            } else {
+                v = in[(long long)(rhs0 + j) * ld_in + pos];
+            }
+        }
+        xs[k * NT + j] = v;
     }
     __syncthreads();
     const long long out_base = p.aout * A + p.bout * B;
@@ -89,14 +110,28 @@ __global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const floa
         const int c = o / p.bsz_out, x = o - c * p.bsz_out;
         const long long pos = (out_base + c * p.sout) * p.bsz_out + x;
 #pragma unroll
-        for (int j = 0; j < NT; ++j)
-            if (j < nt) out[(long long)(rhs0 + j) * ld_out + pos] = acc[j];
+        for (int j = 0; j < NT; ++j) {
+            if (j >= nt) continue;
+            if (p.out_planar) {
+                float *f = reinterpret_cast<float *>(out) + planar_at(p.R, rhs0 + j, pos);
+                f[0] = acc[j].x;
+                f[128] = acc[j].y;
+            } else {
+                out[(long long)(rhs0 + j) * ld_out + pos] = acc[j];
+            }
+        }
     }
 }
 
 struct HostPass {
     Pass p;
     float2 *d = nullptr;
+    // tensor-core form of the same level (batches of 32 or more vectors)
+    bool tc = false;
+    int parts = 1, chunks = 1, Nc = 0, Kc = 0;   // output parts of Nc, K-chunks of Kc
+    float *dtc = nullptr;                        // [Re F; Im F] per (group, part, chunk)
+    uint16_t *d16 = nullptr;                     // the same split into BF16 parts (BF16 rungs)
+    int d16_parts = 0;
 };
 
 }  // namespace
@@ -109,6 +144,10 @@ struct bf_quad_s {
     float2 *ws[2] = {nullptr, nullptr};
     size_t device_bytes = 0;
     int num_sms = 1;
+    bool tc = false;          // tensor-core passes built (nrhs_max >= 32)
+    int tc_min = 32;          // smallest chunk of vectors the tensor-core path serves
+    int tc_split = 3, tc_bf16 = 0;
+    unsigned *d_err = nullptr;
 };
 
 namespace {
@@ -188,6 +227,27 @@ bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::
             if (p.Kin > bfq::kMaxStack || p.Nout > bfq::kMaxStack) return BF_ERR_UNSUPPORTED;
             const long long ngroups = nA * nB;
             const size_t per = (size_t)p.Kin * p.Nout;
+            // Tensor-core form: every pass but the two that touch the caller's vectors,
+            // when the stack splits into parts / K-chunks of at most 64 that are
+            // multiples of 16.
+            bfq::HostPass hp;
+            hp.p = p;
+            const bool edge = (half == 0 && s == 0) || (half == 1 && s == L - h - 1);
+            auto split64 = [](int D, int &n, int &each) {
+                n = (D + 63) / 64;
+                each = D / n;
+                return D % n == 0 && each % 16 == 0;
+            };
+            hp.tc = Q.tc && !edge && split64(p.Kin, hp.chunks, hp.Kc) && split64(p.Nout, hp.parts, hp.Nc);
+            const size_t tper = (size_t)2 * hp.Nc * hp.Kc;   // floats per (group, part, chunk) block
+            std::vector<float> tch;
+            if (hp.tc) {
+                try {
+                    tch.assign(tper * hp.parts * hp.chunks * ngroups, 0.f);
+                } catch (const std::bad_alloc &) {
+                    return BF_ERR_NOMEM;
+                }
+            }
             std::vector<float2> host;
             try {
                 host.resize(per * ngroups);
@@ -241,9 +301,18 @@ bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::
                         const cd v = blk[(size_t)o * p.Kin + k];
                         Fg[(size_t)k * p.Nout + o] = make_float2((float)v.real(), (float)v.imag());
                     }
+                if (!hp.tc) return;
+                // [Re F; Im F] of rows part*Nc.., columns chunk*Kc.. in the MMA operand layout
+                for (int pp = 0; pp < hp.parts; ++pp)
+                    for (int cc = 0; cc < hp.chunks; ++cc) {
+                        float *tb = tch.data() + ((g * hp.parts + pp) * hp.chunks + cc) * tper;
+                        for (int n = 0; n < 2 * hp.Nc; ++n)
+                            for (int k = 0; k < hp.Kc; ++k) {
+                                const cd v = blk[(size_t)(pp * hp.Nc + n % hp.Nc) * p.Kin + cc * hp.Kc + k];
+                                tb[bfint::tc_boff(n, k, 2 * hp.Nc) / 4] = (float)(n < hp.Nc ? v.real() : v.imag());
+                            }
+                    }
             });
-            bfq::HostPass hp;
-            hp.p = p;
             if (cudaMalloc(&hp.d, host.size() * sizeof(float2)) != cudaSuccess) {
                 cudaGetLastError();
                 return BF_ERR_NOMEM;
@@ -253,6 +322,17 @@ bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::
             if (cudaMemcpy(hp.d, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
                 return qfail(cudaErrorUnknown);
             out.back().p.F = hp.d;
+            if (hp.tc) {
+                if (cudaMalloc(&out.back().dtc, tch.size() * sizeof(float)) != cudaSuccess) {
+                    cudaGetLastError();
+                    out.back().dtc = nullptr;
+                    return BF_ERR_NOMEM;
+                }
+                Q.device_bytes += tch.size() * sizeof(float);
+                if (cudaMemcpy(out.back().dtc, tch.data(), tch.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                    return qfail(cudaErrorUnknown);
+            }
         }
     }
     return BF_OK;
@@ -261,9 +341,14 @@ bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::
 void free_quad(bf_quad_s *Q) {
     if (!Q) return;
     for (auto *d : {&Q->fwd, &Q->adj})
-        for (auto &hp : *d) cudaFree(hp.d);
+        for (auto &hp : *d) {
+            cudaFree(hp.d);
+            cudaFree(hp.dtc);
+            cudaFree(hp.d16);
+        }
     cudaFree(Q->ws[0]);
     cudaFree(Q->ws[1]);
+    cudaFree(Q->d_err);
     delete Q;
 }
 
@@ -326,10 +411,18 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&Q->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(1, std::atoi(e));
+    Q->tc = Q->nrhs_max >= Q->tc_min;
+    if (Q->tc && bfint::tc_prepare() != cudaSuccess) {
+        delete Q;
+        return qfail(cudaErrorUnknown);
+    }
     bf_status st = build_direction(*Q, *f, false, Q->fwd);
     if (st == BF_OK) st = build_direction(*Q, *f, true, Q->adj);
     if (st == BF_OK) {
-        const size_t ws = (size_t)Q->Rmax * Q->nrhs_max * sizeof(float2);
+        // planar 128-vector tiles on the tensor-core path: room for whole tiles
+        const long long cols = Q->tc ? (Q->nrhs_max + 127) / 128 * 128 : Q->nrhs_max;
+        const size_t ws = (size_t)Q->Rmax * cols * sizeof(float2);
         for (auto &w : Q->ws)
             if (st == BF_OK && cudaMalloc(&w, ws) != cudaSuccess) {
                 cudaGetLastError();
@@ -337,6 +430,12 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
                 st = BF_ERR_NOMEM;
             }
         if (st == BF_OK) Q->device_bytes += 2 * ws;
+        if (st == BF_OK && cudaMalloc(&Q->d_err, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            Q->d_err = nullptr;
+            st = BF_ERR_NOMEM;
+        }
+        if (st == BF_OK && cudaMemset(Q->d_err, 0, sizeof(unsigned)) != cudaSuccess) st = qfail(cudaErrorUnknown);
     }
     if (st == BF_OK && cudaStreamSynchronize(stream) != cudaSuccess) st = qfail(cudaErrorUnknown);
     if (st != BF_OK) {
@@ -362,17 +461,104 @@ bf_status bf_quad_apply(bf_quad Q, const void *in, void *out, int nrhs, long lon
         const int nc = std::min(Q->nrhs_max, nrhs - k0);
         const float2 *src = static_cast<const float2 *>(in) + (long long)k0 * ld;
         float2 *dst = static_cast<float2 *>(out) + (long long)k0 * ld;
+        const bool tc = Q->tc && nc >= Q->tc_min;   // planar tiles between the passes, tensor cores where built
         for (int ps = 0; ps < np; ++ps) {
+            const bfq::HostPass &hp = D[ps];
             const float2 *pin = ps == 0 ? src : Q->ws[(ps - 1) & 1];
             float2 *pout = ps == np - 1 ? dst : Q->ws[ps & 1];
             const long long lin = ps == 0 ? ld : Q->Rmax, lout = ps == np - 1 ? ld : Q->Rmax;
-            if (run_pass(D[ps].p, pin, lin, pout, lout, nc, stream) != cudaSuccess) return qfail(cudaErrorUnknown);
+            cudaError_t e;
+            if (tc && hp.tc) {
+                bfint::QuadTc q{};
+                q.fac = hp.dtc;
+                q.fac16 = hp.d16;
+                q.in = pin;
+                q.out = pout;
+                q.R = Q->Rmax;
+                q.err = Q->d_err;
+                q.ain = hp.p.ain, q.bin = hp.p.bin, q.sin = hp.p.sin;
+                q.aout = hp.p.aout, q.bout = hp.p.bout, q.sout = hp.p.sout;
+                q.bszi = hp.p.bsz_in, q.bszo = hp.p.bsz_out, q.nB = hp.p.nB;
+                q.ngroups = hp.p.nA * hp.p.nB;
+                q.parts = hp.parts, q.chunks = hp.chunks, q.Kin = hp.Kc, q.Nout = hp.Nc, q.nrhs = nc;
+                q.split = Q->tc_split, q.bf16 = Q->tc_bf16;
+                e = bfint::quad_tc_launch(q, Q->num_sms, stream);
+            } else {
+                bfq::Pass pp = hp.p;
+                pp.in_planar = tc && ps > 0;
+                pp.out_planar = tc && ps < np - 1;
+                pp.R = Q->Rmax;
+                e = run_pass(pp, pin, lin, pout, lout, nc, stream);
+            }
+            if (e != cudaSuccess) return qfail(e);
         }
     }
     return BF_OK;
 }
 
 size_t bf_quad_device_bytes(bf_quad Q) { return Q ? Q->device_bytes : 0; }
+
+int bf_quad_tc_passes(bf_quad Q) {
+    int n = 0;
+    if (Q)
+        for (const auto &hp : Q->fwd) n += hp.tc ? 1 : 0;
+    return n;
+}
+
+bf_status bf_quad_check(bf_quad Q, cudaStream_t stream) {
+    if (!Q) return BF_ERR_INVALID;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return qfail(cudaErrorUnknown);
+    unsigned e = 0;
+    if (cudaMemcpy(&e, Q->d_err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return qfail(cudaErrorUnknown);
+    if (e && cudaMemset(Q->d_err, 0, sizeof(unsigned)) != cudaSuccess) return qfail(cudaErrorUnknown);
+    return e ? BF_ERR_TIMEOUT : BF_OK;
+}
+
+bf_status bf_quad_set_precision(bf_quad Q, int precision) {
+    if (!Q) return BF_ERR_INVALID;
+    int split, bf16;
+    switch (precision) {
+    case BF_PREC_FP32: split = 3; bf16 = 0; break;
+    case BF_PREC_TF32: split = 1; bf16 = 0; break;
+    case BF_PREC_BF16X3: split = 3; bf16 = 1; break;
+    case BF_PREC_BF16: split = 1; bf16 = 1; break;
+    case BF_PREC_BF16X6: split = 6; bf16 = 1; break;
+    default: return BF_ERR_INVALID;
+    }
+    const int parts = bf16 ? (split == 6 ? 3 : split == 3 ? 2 : 1) : 0;
+    std::vector<bfq::HostPass *> todo;
+    for (auto *D : {&Q->fwd, &Q->adj})
+        for (auto &hp : *D)
+            if (hp.tc && hp.d16_parts != parts) todo.push_back(&hp);
+    auto part_bytes = [](const bfq::HostPass &hp) {
+        return (size_t)hp.p.nA * hp.p.nB * hp.parts * hp.chunks * 2 * hp.Nc * hp.Kc * sizeof(uint16_t);
+    };
+    std::vector<uint16_t *> fresh(todo.size(), nullptr);   // allocate all first: on failure the plan is unchanged
+    if (parts > 0)
+        for (size_t i = 0; i < todo.size(); ++i)
+            if (cudaMalloc(&fresh[i], part_bytes(*todo[i]) * parts) != cudaSuccess) {
+                cudaGetLastError();
+                for (uint16_t *q : fresh) cudaFree(q);
+                return BF_ERR_NOMEM;
+            }
+    if (cudaDeviceSynchronize() != cudaSuccess) return qfail(cudaErrorUnknown);
+    for (size_t i = 0; i < todo.size(); ++i) {
+        bfq::HostPass &hp = *todo[i];
+        cudaFree(hp.d16);
+        Q->device_bytes -= part_bytes(hp) * hp.d16_parts;
+        hp.d16 = fresh[i];
+        hp.d16_parts = parts;
+        if (parts == 0) continue;
+        Q->device_bytes += part_bytes(hp) * parts;
+        if (bfint::bf16_split(hp.dtc, hp.d16, (long long)hp.p.nA * hp.p.nB * hp.parts * hp.chunks, 2 * hp.Nc, hp.Kc,
+                              parts, Q->num_sms) != cudaSuccess)
+            return qfail(cudaErrorUnknown);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return qfail(cudaErrorUnknown);
+    Q->tc_split = split;
+    Q->tc_bf16 = bf16;
+    return BF_OK;
+}
 
 int bf_quad_passes(bf_quad Q) { return Q ? (int)Q->fwd.size() : 0; }
 

@@ -92,8 +92,8 @@ constexpr uint32_t kStageBytes = (uint32_t)NR * kPointRow;                   // 
 constexpr uint32_t kTrBytes = 32u * 64u;                                     // per-warp transpose tile
 constexpr size_t kSmemBytes = 2ull * kStages * kSlotBytes + kStageBytes + kEpiWarps * kTrBytes + 256;
 
-enum LoadKind : int { LD_POINTS = 0, LD_SLOTS = 1, LD_GATHER = 2 };
-enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2 };
+enum LoadKind : int { LD_POINTS = 0, LD_SLOTS = 1, LD_GATHER = 2, LD_QUAD = 3 };
+enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2, ST_QUAD = 3 };
 
 // Passed as a __grid_constant__ kernel parameter: the TMA reads the tensor
 // map from parameter space.
@@ -116,6 +116,13 @@ struct alignas(64) TcParams {
     int split;              // products per real product: 1 plain; 3 hi/lo split; 6 (BF16 only) hi/mid/lo split
     int bf16;               // operand type: 0 TF32 (kind::tf32, K = 8), 1 BF16 (kind::f16, K = 16)
     int use_tmap;           // LD_POINTS: load the tile by tensor-map copies (else one copy per row)
+    // LD_QUAD / ST_QUAD: one level of a 2D (quadtree) factorization.  Group g = A q_nB + B
+    // reads the four blocks q_ain A + q_bin B + c q_sin (c = 0..3, q_bszi positions each)
+    // and writes q_aout A + q_bout B + c q_sout (q_bszo each).  A work item is
+    // (group, output part, RHS tile): Nout of the group's 4 q_bszo outputs, accumulated
+    // over q_chunks K-chunks of Kin inputs each (consecutive sub-items of one CTA).
+    long long q_ain, q_bin, q_sin, q_aout, q_bout, q_sout;
+    int q_bszi, q_bszo, q_nB, q_ngroups, q_parts, q_chunks;
 };
 
 // Byte offset of (row n, col k) in a K-major no-swizzle operand of `rows`
@@ -267,15 +274,45 @@ __device__ __forceinline__ void warp_arrive(uint64_t *bar) {
 
 struct Item {
     int n, g, t, nt;
+    int part, chunk;   // LD_QUAD: output part and K-chunk (0 otherwise)
+    bool last;         // last K-chunk: the accumulators hold the item's result
+    long long blk;     // index of the item's block F
 };
-__device__ __forceinline__ Item decode(const TcParams &p, int item, int ntiles) {
+__device__ __forceinline__ int nchunks(const TcParams &p) { return p.q_chunks > 1 ? p.q_chunks : 1; }
+__device__ __forceinline__ int nwork(const TcParams &p, int ntiles) {
+    return (p.load_kind == LD_QUAD ? p.q_ngroups * p.q_parts : p.m * p.ngroups) * ntiles;
+}
+// Work item of this CTA's sub-item s: work items blockIdx.x, + gridDim.x, ..., each
+// taken as nchunks consecutive sub-items (its K-chunks).
+__device__ __forceinline__ int sub_item(const TcParams &p, int s) { return blockIdx.x + (s / nchunks(p)) * gridDim.x; }
+__device__ __forceinline__ Item decode(const TcParams &p, int item, int chunk, int ntiles) {
     Item it;
     it.t = item % ntiles;
     const int ng = item / ntiles;
-    it.n = ng / p.ngroups;
-    it.g = ng - it.n * p.ngroups;
+    it.chunk = chunk;
+    it.last = chunk == nchunks(p) - 1;
+    if (p.load_kind == LD_QUAD) {
+        it.n = 0;
+        it.g = ng / p.q_parts;
+        it.part = ng - it.g * p.q_parts;
+        it.blk = (long long)ng * nchunks(p) + chunk;
+    } else {
+        it.n = ng / p.ngroups;
+        it.g = ng - it.n * p.ngroups;
+        it.part = 0;
+        it.blk = (long long)it.n * p.ngroups + it.g;
+    }
     it.nt = min(NR, p.nrhs - it.t * NR);
     return it;
+}
+// LD_QUAD / ST_QUAD: first input / output block index of the item's group.
+__device__ __forceinline__ long long quad_in_base(const TcParams &p, const Item &w) {
+    const int A = w.g / p.q_nB, B = w.g - A * p.q_nB;
+    return p.q_ain * A + p.q_bin * B;
+}
+__device__ __forceinline__ long long quad_out_base(const TcParams &p, const Item &w) {
+    const int A = w.g / p.q_nB, B = w.g - A * p.q_nB;
+    return p.q_aout * A + p.q_bout * B;
 }
 
 // Position (in the intermediate) of the first entry of local slot j's r-block.
@@ -313,21 +350,33 @@ __device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
-// Global sources of an item's block F and input tile: `fn(src, bytes)` per copy,
-// the tile's copies distributed over the warp's lanes.
+// The copies of an item's input tile: `fn(staging offset, src, bytes)` per copy,
+// distributed over the warp's lanes.
 template <class Fn>
 __device__ __forceinline__ void tile_copies(const TcParams &p, const Item &w, int lane, Fn fn) {
     if (p.load_kind == LD_POINTS) {
         const float2 *src = p.in + (long long)(w.t * NR) * p.ld_in + ((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0;
-        for (int row = lane; row < w.nt; row += 32) fn(row, src + (long long)row * p.ld_in, (uint32_t)p.Kin * 8u);
+        for (int row = lane; row < w.nt; row += 32)
+            fn((uint32_t)row * kPointRow, src + (long long)row * p.ld_in, (uint32_t)p.Kin * 8u);
+    } else if (p.load_kind == LD_QUAD) {
+        // inputs chunk*Kin .. +Kin of the group's stack: runs inside its four blocks
+        const int k0 = w.chunk * p.Kin, c0 = k0 / p.q_bszi, c1 = (k0 + p.Kin - 1) / p.q_bszi;
+        const long long base = quad_in_base(p, w);
+        for (int c = c0 + lane; c <= c1; c += 32) {
+            const int ka = max(k0, c * p.q_bszi), kb = min(k0 + p.Kin, (c + 1) * p.q_bszi);
+            const long long pos = (base + c * p.q_sin) * p.q_bszi + (ka - c * p.q_bszi);
+            fn((uint32_t)(ka - k0) * NR * 8u, p.in + ((long long)w.t * p.R + pos) * NR, (uint32_t)(kb - ka) * NR * 8u);
+        }
     } else {
         for (int j = lane; j < p.G; j += 32)
-            fn(j, p.in + ((long long)w.t * p.R + slot_pos(p, w, j)) * NR, (uint32_t)p.r * NR * 8u);
+            fn((uint32_t)j * p.r * NR * 8u, p.in + ((long long)w.t * p.R + slot_pos(p, w, j)) * NR,
+               (uint32_t)p.r * NR * 8u);
     }
 }
 __device__ __forceinline__ uint32_t tile_bytes(const TcParams &p, const Item &w) {
     if (p.load_kind == LD_POINTS)
         return p.use_tmap ? (uint32_t)(p.Kin / 16) * kBoxBytes : (uint32_t)p.Kin * 8u * (uint32_t)w.nt;
+    if (p.load_kind == LD_QUAD) return (uint32_t)p.Kin * NR * 8u;
     return (uint32_t)p.r * NR * 8u * (uint32_t)p.G;
 }
 // Tensor-map coordinates of an LD_POINTS item: x (floats) of its first point, y (row) of its first RHS.
@@ -335,13 +384,13 @@ __device__ __forceinline__ int points_x(const TcParams &p, const Item &w) {
     return (int)(2 * (((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0));
 }
 __device__ __forceinline__ const float *block_src(const TcParams &p, const Item &w) {
-    return p.fac + ((long long)w.n * p.ngroups + w.g) * (2ll * p.Nout * p.Kin);
+    return p.fac + w.blk * (2ll * p.Nout * p.Kin);
 }
 // BF16 rungs: split parts per block and bytes per part.
 __device__ __forceinline__ int bf16_parts(const TcParams &p) { return p.split == 6 ? 3 : p.split == 3 ? 2 : 1; }
 __device__ __forceinline__ uint32_t part_bytes(const TcParams &p) { return 2u * p.Nout * p.Kin * 2u; }
 __device__ __forceinline__ const uint16_t *block_src16(const TcParams &p, const Item &w) {
-    return p.fac16 + ((long long)w.n * p.ngroups + w.g) * (2ll * p.Nout * p.Kin) * bf16_parts(p);
+    return p.fac16 + w.blk * (2ll * p.Nout * p.Kin) * bf16_parts(p);
 }
 // Bytes of one item's block as streamed: FP32, or the BF16 parts.
 __device__ __forceinline__ uint32_t block_bytes(const TcParams &p) {
@@ -355,8 +404,8 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
     const int lane = threadIdx.x & 31;
     const uint32_t ubytes = block_bytes(p);
     uint32_t nf = 0, nx = 0;   // factor copies / staging groups issued
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const Item w = decode(p, item, ntiles);
+    for (int sub = 0; sub_item(p, sub) < nitems; ++sub) {
+        const Item w = decode(p, sub_item(p, sub), sub % nchunks(p), ntiles);
         const uint32_t slot = nf % kStages, use = nf / kStages;
         bool ok = true;
         if (lane == 0) {
@@ -383,18 +432,16 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
         if (p.load_kind == LD_POINTS && p.use_tmap) {
             if (lane < p.Kin / 16)
                 tma_load_2d(s.xs + (size_t)lane * kBoxBytes, &p.tmap, points_x(p, w) + 32 * lane, w.t * NR, s.xfull);
-        } else if (p.load_kind == LD_POINTS)
-            tile_copies(p, w, lane, [&](int i, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + (size_t)i * kPointRow, src, b, s.xfull); });
-        else
-            tile_copies(p, w, lane, [&](int i, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + (size_t)i * b, src, b, s.xfull); });
+        } else
+            tile_copies(p, w, lane, [&](uint32_t off, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + off, src, b, s.xfull); });
         ++nx;
-        if (item + (int)gridDim.x < nitems) {   // next item of this CTA: into L2
-            const Item w2 = decode(p, item + gridDim.x, ntiles);
+        if (sub_item(p, sub + 1) < nitems) {   // next item of this CTA: into L2
+            const Item w2 = decode(p, sub_item(p, sub + 1), (sub + 1) % nchunks(p), ntiles);
             if (lane == 0) prefetch_l2(p.bf16 ? (const void *)block_src16(p, w2) : (const void *)block_src(p, w2), ubytes);
             if (p.load_kind == LD_POINTS && p.use_tmap) {
                 if (lane < p.Kin / 16) prefetch_tile_2d(&p.tmap, points_x(p, w2) + 32 * lane, w2.t * NR);
             } else {
-                tile_copies(p, w2, lane, [&](int, const void *src, uint32_t b) { prefetch_l2(src, b); });
+                tile_copies(p, w2, lane, [&](uint32_t, const void *src, uint32_t b) { prefetch_l2(src, b); });
             }
         }
     }
@@ -412,7 +459,7 @@ __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitem
     const int lane = threadIdx.x & 31;
     const int n4 = 2 * p.Nout * p.Kin / 4;
     uint32_t it = 0;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+    for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
         const uint32_t slot = it % kStages;
         const bool ok = warp_wait(&s.full[slot], (it / kStages) & 1, s.abort_flag, p.err);
         if (ok && !p.bf16) {   // (BF16 rungs stream blocks already split: nothing to do)
@@ -437,7 +484,8 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
     const uint32_t lbo = (uint32_t)(rows >> 3) * 128u;
     const uint32_t idesc = idesc_tf32(rows);
     uint32_t it = 0;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
+    for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
+        const uint32_t acc0 = (sub % nchunks(p)) ? 1u : 0u;   // later K-chunks accumulate
         const uint32_t slot = it % kStages;
         const uint32_t b1 = bfk::smem_u32(s.ring) + slot * kSlotBytes;
         const uint32_t bl = bfk::smem_u32(s.blo) + slot * kSlotBytes;
@@ -459,7 +507,7 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
                 const int nk = p.Kin / 16;
                 for (int kk = 0; kk < nk; ++kk) {
                     const uint32_t bo = (uint32_t)(2 * kk) * lbo, c = (uint32_t)(8 * kk);
-                    mma_ts_bf16(d, xh + c, sdesc(blow + bo, lbo, 128), idesc16, kk ? 1u : 0u);
+                    mma_ts_bf16(d, xh + c, sdesc(blow + bo, lbo, 128), idesc16, (kk || acc0) ? 1u : 0u);
                     mma_ts_bf16(d, xl + c, sdesc(bhi + bo, lbo, 128), idesc16, 1);
                     mma_ts_bf16(d, xh + 32 + c, sdesc(bmid + bo, lbo, 128), idesc16, 1);
                 }
@@ -478,14 +526,14 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
                     for (int kk = 0; kk < p.Kin / 16; ++kk) {
                         const uint32_t bo = (uint32_t)(2 * kk) * lbo;
                         const uint32_t c = (uint32_t)(8 * kk);
-                        mma_ts_bf16(d, xh + c, sdesc(blow + bo, lbo, 128), idesc16, first ? 0u : 1u);
+                        mma_ts_bf16(d, xh + c, sdesc(blow + bo, lbo, 128), idesc16, first ? acc0 : 1u);
                         mma_ts_bf16(d, xl + c, sdesc(bhi + bo, lbo, 128), idesc16, 1);
                         first = false;
                     }
                 }
                 for (int kk = 0; kk < p.Kin / 16; ++kk) {
                     const uint32_t bo = (uint32_t)(2 * kk) * lbo;
-                    mma_ts_bf16(d, xh + (uint32_t)(8 * kk), sdesc(bhi + bo, lbo, 128), idesc16, first ? 0u : 1u);
+                    mma_ts_bf16(d, xh + (uint32_t)(8 * kk), sdesc(bhi + bo, lbo, 128), idesc16, first ? acc0 : 1u);
                     first = false;
                 }
             } else if (ok) {
@@ -498,14 +546,14 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
                     for (int kk = 0; kk < p.Kin / 8; ++kk) {
                         const uint32_t bo = (uint32_t)(2 * kk) * lbo;
                         const uint32_t c = (uint32_t)(8 * kk);
-                        mma_ts(d, xh + c, sdesc(bl + bo, lbo, 128), idesc, first ? 0u : 1u);
+                        mma_ts(d, xh + c, sdesc(bl + bo, lbo, 128), idesc, first ? acc0 : 1u);
                         mma_ts(d, xl + c, sdesc(b1 + bo, lbo, 128), idesc, 1);
                         first = false;
                     }
                 }
                 for (int kk = 0; kk < p.Kin / 8; ++kk) {
                     const uint32_t bo = (uint32_t)(2 * kk) * lbo;
-                    mma_ts(d, xh + (uint32_t)(8 * kk), sdesc(b1 + bo, lbo, 128), idesc, first ? 0u : 1u);
+                    mma_ts(d, xh + (uint32_t)(8 * kk), sdesc(b1 + bo, lbo, 128), idesc, first ? acc0 : 1u);
                     first = false;
                 }
             }
@@ -630,6 +678,18 @@ __device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const I
         }
         if (p.store_kind == ST_POINTS) {
             store_points8(p, s, w, q, o, re, im);
+        } else if (p.store_kind == ST_QUAD) {
+            if (live) {
+                const long long base = quad_out_base(p, w);
+                float *dst = reinterpret_cast<float *>(p.out) + (long long)w.t * p.R * 2 * NR + mlane;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int oo = w.part * p.Nout + o + i, c = oo / p.q_bszo;
+                    const long long pos = (base + c * p.q_sout) * p.q_bszo + (oo - c * p.q_bszo);
+                    dst[pos * 2 * NR] = re[i];
+                    dst[pos * 2 * NR + NR] = im[i];
+                }
+            }
         } else if (live) {
             const int j = o / p.r, kk = o - j * p.r;
             const int ps = slot_of(p, w.g, j);
@@ -726,7 +786,7 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
     tc_fence_after();
     const uint32_t tmem = *s.tmem_slot;
     const int ntiles = (p.nrhs + NR - 1) / NR;
-    const int nitems = p.m * p.ngroups * ntiles;
+    const int nitems = nwork(p, ntiles);
     if (warp == kProdWarp) {
         producer(p, s, ntiles, nitems);
     } else if (warp == kPrepWarp) {
@@ -740,13 +800,13 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
         uint32_t it = 0;
         Item prev{};
         Acc acc;
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++it) {
-            const Item w = decode(p, item, ntiles);
+        for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
+            const Item w = decode(p, sub_item(p, sub), sub % nchunks(p), ntiles);
             bool okd = false;
-            if (it > 0) {   // item it-1: D -> registers (its E group is running)
+            if (it > 0) {   // item it-1: D -> registers (its E group is running) once its last K-chunk is in
                 okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
                 tc_fence_after();
-                if (okd) read_d(p, lb, hf, acc);
+                if (okd && prev.last) read_d(p, lb, hf, acc);
             }
             const bool okx = warp_wait(s.xfull, it & 1, s.abort_flag, p.err);
             if (okx) convert(p, s, lb, mlane, hf, 0);
@@ -755,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
             if (it > 0) {   // item it-1: E, combine, store (item it's D group is running)
                 const bool oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
                 tc_fence_after();
-                if (okd && oke) finish(p, s, prev, lb, q, mlane, hf, acc);
+                if (okd && oke && prev.last) finish(p, s, prev, lb, q, mlane, hf, acc);
             }
             if (okx) convert(p, s, lb, mlane, hf, 1);
             tc_fence_before();

@@ -142,3 +142,42 @@ def test_quad_argument_errors(bf):
     with pytest.raises(bf.BfError) as e:
         bf.bf_quad_create(F)
     assert e.value.status == bf.BF_ERR_INVALID
+
+
+@pytest.mark.parametrize("L,n0,r,nrhs", [(6, 1, 24, 128), (4, 4, 24, 40), (4, 16, 8, 33), (6, 4, 16, 160)])
+def test_quad_tensor_core_rungs(bf, L, n0, r, nrhs):
+    """Chunks of 32 or more vectors run the inner levels on the tensor-core
+    core (output parts and K-chunks of at most 64, planar tiles between the
+    levels).  Every precision rung, forward and adjoint, against the FP64
+    oracle: 3xTF32 and the BF16 three-way split within the FP32 tolerance,
+    the others in their bands; and 3xTF32 against the CUDA-core path of the
+    same plan (chunks below 32 vectors)."""
+    from bfinputs import complex_normal
+    from bfinputs.quad import synthetic_quad_factors
+    from oracle import quad as Q
+    F = synthetic_quad_factors(L, n0, r, seed=500 + r, dtype=np.complex64)
+    plan = bf.bf_quad_create(F, nrhs_max=nrhs)
+    assert 0 < bf.bf_quad_tc_passes(plan) <= L - 2
+    g = complex_normal((nrhs, F.N), seed=600 + L, dtype=np.complex64)
+    cols = [0, nrhs // 2, nrhs - 1]
+    for adjoint in (False, True):
+        ref = (Q.bf_adjoint if adjoint else Q.bf_apply)(F, g[cols].T).T
+        errs = {}
+        for prec in (bf.BF_PREC_FP32, bf.BF_PREC_TF32, bf.BF_PREC_BF16X6, bf.BF_PREC_BF16X3, bf.BF_PREC_BF16):
+            bf.bf_quad_set_precision(plan, prec)
+            out = _gpu(bf, plan, g, adjoint)
+            bf.bf_quad_check(plan)
+            errs[prec] = _rel(out[cols], ref)
+        assert errs[bf.BF_PREC_FP32] < TOL and errs[bf.BF_PREC_BF16X6] < TOL, errs
+        assert 1e-4 < errs[bf.BF_PREC_TF32] < 1e-2, errs
+        assert 1e-6 < errs[bf.BF_PREC_BF16X3] < 5e-5, errs
+        assert 1e-3 < errs[bf.BF_PREC_BF16] < 3e-2, errs
+        bf.bf_quad_set_precision(plan, bf.BF_PREC_FP32)
+        tc = _gpu(bf, plan, g, adjoint)
+        x = torch.from_numpy(g).cuda()
+        y = torch.empty_like(x)
+        for k0 in range(0, nrhs, 16):                       # 16 at a time: the CUDA-core levels
+            bf.bf_quad_apply(plan, x[k0:k0 + 16], y[k0:k0 + 16], adjoint=adjoint)
+        torch.cuda.synchronize()
+        assert _rel(tc, y.cpu().numpy()) < TOL
+    plan.destroy()
