@@ -348,31 +348,31 @@ def fp32_fma_peak_tflops(dev) -> float:
 def quad_line(dev, stream):
     """The 2D workload: a 256 x 256 grid (N = 65536), quadtrees of depth 8 with
     one point per leaf, rank 24 (level ranks 24, 24, 16, 4, 1), seeded
-    synthetic factor values; apply + adjoint of 1 and of 128 vectors through
-    the level kernels (FP32 on CUDA cores)."""
+    synthetic factor values; apply + adjoint of 1 vector (CUDA-core level
+    kernels, HBM-bound) and of 128 (the six inner levels on the tensor-core
+    core), each precision rung beside the FP32 CUDA-core path of the same
+    plan (16 vectors per call) on the same vectors."""
     import numpy as np
     import torch
 
     from paper_1502_01379_gb300 import capi
     from bfinputs import complex_normal
-    from bfinputs.quad import QUAD_CONFIGS, synthetic_quad_factors
+    from bfinputs.quad import QUAD_CONFIGS, quad_sizes, synthetic_quad_factors
     cfg = QUAD_CONFIGS["fio2d_n65536_r24"]
-    F = synthetic_quad_factors(cfg["L"], cfg["n0"], cfg["r"], seed=0, dtype=np.complex64)
+    L, n0, r, nr = cfg["L"], cfg["n0"], cfg["r"], cfg["nrhs"]
+    F = synthetic_quad_factors(L, n0, r, seed=0, dtype=np.complex64)
     entries = F.nentries() - F.S.size            # complex entries of the dense group blocks (S folded in)
-    plan = capi.bf_quad_create(F, nrhs_max=cfg["nrhs"])
+    plan = capi.bf_quad_create(F, nrhs_max=nr)
     res = {"workload": "2D: butterfly factorization on quadtrees of a 2D-FIO-shaped N=65536 matrix (256x256 grid), "
                        "L=8, leaf=1, r=24, seeded synthetic factor values; step = apply + adjoint",
            "factor_entries": int(entries), "plan_device_gb": capi.bf_quad_device_bytes(plan) / 1e9,
-           "launches_per_apply": capi.bf_quad_passes(plan)}
+           "launches_per_apply": capi.bf_quad_passes(plan), "tensor_core_levels": capi.bf_quad_tc_passes(plan)}
     peak, peak_src = load_peaks()
-    for nrhs in (1, cfg["nrhs"]):
-        g = torch.from_numpy(complex_normal((nrhs, F.N), seed=40 + nrhs, dtype=np.complex64)).to(dev)
-        u, v = torch.empty_like(g), torch.empty_like(g)
 
+    def timed(g, u, v, reps):
         def step():
             capi.bf_quad_apply(plan, g, u, stream=stream)
             capi.bf_quad_apply(plan, u, v, adjoint=True, stream=stream)
-        reps = 20 if nrhs == 1 else 5
         for _ in range(3):
             step()
         torch.cuda.synchronize()
@@ -382,22 +382,56 @@ def quad_line(dev, stream):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        ent = {"vectors_per_s": 2 * nrhs / (ms / 1e3), "ms_per_apply": ms / 2}
-        if nrhs == 1:
-            alg = entries * 8 + 2 * F.N * 8
-            ent["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 2 / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                               "frac": alg / (ms / 2 / 1e3) / 1e9 / peak, "peak_source": peak_src,
-                               "bytes_note": "per apply: every dense group block once (complex64) + in/out vectors"}
-        else:
-            flops = 8.0 * entries * nrhs
-            fp = fp32_fma_peak_tflops(dev)
-            ent["roofline"] = {"bound": "fma", "achieved": flops / (ms / 2 / 1e3) / 1e12, "peak": fp,
-                               "unit": "TFLOP/s", "frac": flops / (ms / 2 / 1e3) / 1e12 / fp,
-                               "peak_source": "derived: SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                               "flops_note": "8 real flops per complex multiply-add of every dense group block"}
-        res[f"nrhs_{nrhs}"] = ent
-        del g, u, v
+        capi.bf_quad_check(plan)
+        return e0.elapsed_time(e1) / reps
+
+    # 1 vector: a stream over every dense group block
+    g = torch.from_numpy(complex_normal((1, F.N), seed=41, dtype=np.complex64)).to(dev)
+    u, v = torch.empty_like(g), torch.empty_like(g)
+    ms = timed(g, u, v, 20)
+    alg = entries * 8 + 2 * F.N * 8
+    res["nrhs_1"] = {"vectors_per_s": 2 / (ms / 1e3), "ms_per_apply": ms / 2,
+                     "roofline": {"bound": "hbm", "achieved": alg / (ms / 2 / 1e3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": alg / (ms / 2 / 1e3) / 1e9 / peak, "peak_source": peak_src,
+                                  "bytes_note": "per apply: every dense group block once (complex64) + in/out vectors"}}
+    # 128 vectors: inner levels on the tensor cores, every rung
+    g = torch.from_numpy(complex_normal((nr, F.N), seed=40 + nr, dtype=np.complex64)).to(dev)
+    u, v = torch.empty_like(g), torch.empty_like(g)
+    plain = torch.empty_like(g)
+    for k0 in range(0, nr, 16):                 # the FP32 CUDA-core path of the same plan
+        capi.bf_quad_apply(plan, g[k0:k0 + 16], plain[k0:k0 + 16], stream=stream)
+    s = quad_sizes(L, n0, r)
+    rk = s["ranks"]
+    # MMA multiply-adds of one apply's tensor-core levels (merging and splitting
+    # l = h .. L-2), per product: groups x [Re F; Im F] rows x K x 128 RHS, D and E
+    tc_mac = 0
+    for lv in range(L // 2, L - 1):
+        for kin, nout in ((4 * rk[lv + 1], 4 * rk[lv]), (4 * rk[lv], 4 * rk[lv + 1])):
+            tc_mac += (s["nblocks"] // 4) * (2 * nout) * kin * 128 * 2
+    useful = 8.0 * entries * nr
+    tf32_peak, tf32_src = tf32_peak_tflops()
+    rungs = {}
+    for name, prec, products in (("fp32_3xtf32", capi.BF_PREC_FP32, 3), ("tf32", capi.BF_PREC_TF32, 1),
+                                 ("bf16x6", capi.BF_PREC_BF16X6, 6), ("bf16x3", capi.BF_PREC_BF16X3, 3),
+                                 ("bf16", capi.BF_PREC_BF16, 1)):
+        capi.bf_quad_set_precision(plan, prec)
+        ms = timed(g, u, v, 5)
+        capi.bf_quad_apply(plan, g, u, stream=stream)
+        torch.cuda.synchronize()
+        apply_s = ms / 2 / 1e3
+        ent = {"vectors_per_s": 2 * nr / (ms / 1e3), "ms_per_apply": ms / 2,
+               "useful_tflops": useful / apply_s / 1e12,
+               "rel_diff_vs_fp32_cuda_core": rel_diff(u, plain)}
+        if prec in (capi.BF_PREC_FP32, capi.BF_PREC_TF32):
+            issued = 2.0 * tc_mac * products        # 2 flops per multiply-add
+            ent["roofline"] = {"bound": "tensor", "kernel": "bf_tc_kernel (inner levels)",
+                               "achieved": issued / apply_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                               "frac": issued / apply_s / 1e12 / tf32_peak, "peak_source": tf32_src,
+                               "note": "issued MMA flops of the inner levels over the whole apply time "
+                                       "(the two CUDA-core edge levels included in the time)"}
+        rungs[name] = ent
+    capi.bf_quad_set_precision(plan, capi.BF_PREC_FP32)
+    res["nrhs_128"] = rungs
     plan.destroy()
     return res
 

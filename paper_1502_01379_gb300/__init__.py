@@ -8,11 +8,14 @@ fallback: loading raises if the library is missing.
 from .capi import (BF_C64, BF_C128, BF_ERR_CUDA, BF_ERR_INVALID, BF_ERR_NOMEM, BF_ERR_TIMEOUT,
                    BF_ERR_UNSUPPORTED, BF_OK, BfError, Plan, bf_apply, bf_apply_adjoint,
                    bf_plan_check, bf_plan_create, bf_plan_destroy, bf_plan_device_bytes,
-                   bf_plan_kernel_times, bf_plan_set_precision, bf_plan_set_profiling, bf_status_string, load)
+                   bf_plan_kernel_times, bf_plan_set_precision, bf_plan_set_profiling, bf_quad_apply, bf_quad_check,
+                   bf_quad_create, bf_quad_destroy, bf_quad_device_bytes, bf_quad_set_precision, bf_status_string,
+                   load)
 
 __all__ = [
     "BF_C64", "BF_C128", "BF_OK", "BF_ERR_INVALID", "BF_ERR_CUDA", "BF_ERR_NOMEM", "BF_ERR_UNSUPPORTED",
     "BF_ERR_TIMEOUT", "BfError", "Plan", "bf_apply", "bf_apply_adjoint", "bf_plan_check",
     "bf_plan_create", "bf_plan_destroy", "bf_plan_device_bytes", "bf_plan_kernel_times",
-    "bf_plan_set_profiling", "bf_plan_set_precision", "bf_status_string", "load",
+    "bf_plan_set_profiling", "bf_plan_set_precision", "bf_status_string", "load", "bf_quad_create",
+    "bf_quad_apply", "bf_quad_check", "bf_quad_set_precision", "bf_quad_device_bytes", "bf_quad_destroy",
 ]

@@ -61,37 +61,59 @@ __device__ __forceinline__ long long planar_at(long long R, long long j, long lo
     return ((j >> 7) * R + pos) * 256 + (j & 127);
 }
 
+// One vector at a time the kernel streams the factors: 32 registers keep 16
+// blocks of 128 threads (2048 threads) resident for enough loads in flight.
 template <int NT>
-__global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const float2 *__restrict__ in, long long ld_in,
-                                                        float2 *__restrict__ out, long long ld_out, int nrhs) {
-    extern __shared__ float2 xs[];   // [Kin][NT]
+__global__ void __launch_bounds__(128, NT == 1 ? 16 : 1) quad_pass_kernel(const Pass p, const float2 *__restrict__ in, long long ld_in,
+                                                        float2 *__restrict__ out, long long ld_out, int nrhs, int gpb,
+                                                        int tpg) {
+    // gpb consecutive groups per thread block, tpg threads per group (small stacks
+    // share a block so its threads stay busy and its accesses stay contiguous)
+    extern __shared__ float2 xs[];   // [gpb][Kin][NT] inputs, then (planar stores) [gpb][Nout][NT] outputs
     const int ntiles = (nrhs + NT - 1) / NT;
-    const long long g = blockIdx.x / ntiles;
-    const int tile = (int)(blockIdx.x - g * ntiles);
-    const int A = (int)(g / p.nB), B = (int)(g - (long long)A * p.nB);
+    const long long gb = blockIdx.x / ntiles;
+    const int tile = (int)(blockIdx.x - gb * ntiles);
+    const long long ngroups = (long long)p.nA * p.nB, g0 = gb * gpb;
     const int rhs0 = tile * NT, nt = min(NT, nrhs - rhs0);
-    const long long in_base = p.ain * A + p.bin * B;
-    for (int idx = threadIdx.x; idx < p.Kin * NT; idx += blockDim.x) {
-        // consecutive threads: consecutive positions of one vector (RHS-major) or
-        // consecutive vectors at one position (planar)
-        const int j = p.in_planar ? idx % NT : idx / p.Kin, k = p.in_planar ? idx / NT : idx - j * p.Kin;
-        const int c = k / p.bsz_in, x = k - c * p.bsz_in;
-        const long long pos = (in_base + c * p.sin) * p.bsz_in + x;
+    const int per = p.Kin * NT;
+    for (int idx = threadIdx.x; idx < gpb * per; idx += blockDim.x) {
+        // consecutive threads: consecutive positions of consecutive groups of one
+        // vector (RHS-major), or consecutive vectors at one position (planar)
+        int gi, j, k;
+        if (NT >= 8 && p.in_planar) {
+            j = idx % NT;
+            k = (idx / NT) % p.Kin;
+            gi = idx / per;
+        } else {
+            k = idx % p.Kin;
+            gi = (idx / p.Kin) % gpb;
+            j = idx / (p.Kin * gpb);
+        }
+        const long long g = g0 + gi;
         float2 v = make_float2(0.f, 0.f);
-        if (j < nt) {
-            if (p.in_planar) {
+        if (j < nt && g < ngroups) {
+            const int A = (int)(g / p.nB), B = (int)(g - (long long)A * p.nB);
+            const int c = k / p.bsz_in, x = k - c * p.bsz_in;
+            const long long pos = (p.ain * A + p.bin * B + c * p.sin) * p.bsz_in + x;
+            if (NT >= 8 && p.in_planar) {
                 const float *f = reinterpret_cast<const float *>(in) + planar_at(p.R, rhs0 + j, pos);
                 v = make_float2(f[0], f[128]);
             } else {
                 v = in[(long long)(rhs0 + j) * ld_in + pos];
             }
         }
-        xs[k * NT + j] = v;
+        xs[(gi * p.Kin + k) * NT + j] = v;
     }
     __syncthreads();
+    const int gi = threadIdx.x / tpg;
+    const long long g = g0 + gi;
+    const bool active = gi < gpb && g < ngroups;
+    const int A = (int)(g / p.nB), B = (int)(g - (long long)A * p.nB);
     const long long out_base = p.aout * A + p.bout * B;
     const float2 *Fg = p.F + g * (long long)p.Kin * p.Nout;
-    for (int o = threadIdx.x; o < p.Nout; o += blockDim.x) {
+    const float2 *xg = xs + gi * per;
+    float2 *ys = xs + (size_t)gpb * per;   // planar stores: outputs staged here
+    for (int o = threadIdx.x - gi * tpg; active && o < p.Nout; o += tpg) {
         float2 acc[NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -99,7 +121,7 @@ __global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const floa
 #pragma unroll 4
         for (int k = 0; k < p.Kin; ++k) {
             const float2 fv = __ldg(f + (long long)k * p.Nout);
-            const float2 *xk = xs + k * NT;
+            const float2 *xk = xg + k * NT;
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
                 const float2 xv = xk[j];
@@ -107,19 +129,35 @@ __global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const floa
                 acc[j].y = fmaf(fv.x, xv.y, fmaf(fv.y, xv.x, acc[j].y));
             }
         }
+        if (NT >= 8 && p.out_planar) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j) ys[(gi * p.Nout + o) * NT + j] = acc[j];
+            continue;
+        }
         const int c = o / p.bsz_out, x = o - c * p.bsz_out;
         const long long pos = (out_base + c * p.sout) * p.bsz_out + x;
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            if (j >= nt) continue;
-            if (p.out_planar) {
-                float *f = reinterpret_cast<float *>(out) + planar_at(p.R, rhs0 + j, pos);
-                f[0] = acc[j].x;
-                f[128] = acc[j].y;
-            } else {
-                out[(long long)(rhs0 + j) * ld_out + pos] = acc[j];
-            }
-        }
+        for (int j = 0; j < NT; ++j)
+            if (j < nt) out[(long long)(rhs0 + j) * ld_out + pos] = acc[j];
+    }
+    // (planar tiles are used only between the tensor-core levels, with 32 or more
+    // vectors per call and so tiles of NT >= 8)
+    if constexpr (NT < 8) return;
+    if (!p.out_planar) return;
+    // planar stores through shared memory: consecutive threads write consecutive
+    // vectors of one output position (contiguous floats of one tile row)
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < gpb * p.Nout * NT; idx += blockDim.x) {
+        const int j = idx % NT, row = idx / NT, gj = row / p.Nout, oo = row - gj * p.Nout;
+        const long long gg = g0 + gj;
+        if (j >= nt || gg >= ngroups) continue;
+        const int A2 = (int)(gg / p.nB), B2 = (int)(gg - (long long)A2 * p.nB);
+        const int c = oo / p.bsz_out, x = oo - c * p.bsz_out;
+        const long long pos = ((p.aout * A2 + p.bout * B2) + c * p.sout) * p.bsz_out + x;
+        float *f = reinterpret_cast<float *>(out) + planar_at(p.R, rhs0 + j, pos);
+        const float2 v = ys[idx];
+        f[0] = v.x;
+        f[128] = v.y;
     }
 }
 
@@ -356,17 +394,30 @@ template <int NT>
 cudaError_t launch_pass(const bfq::Pass &p, const float2 *in, long long ld_in, float2 *out, long long ld_out, int nrhs,
                         cudaStream_t s) {
     const long long ntiles = (nrhs + NT - 1) / NT;
-    const long long blocks = (long long)p.nA * p.nB * ntiles;
-    const int threads = std::min(128, (p.Nout + 31) / 32 * 32);
-    const size_t smem = (size_t)p.Kin * NT * sizeof(float2);
-    bfq::quad_pass_kernel<NT><<<(unsigned)blocks, threads, smem, s>>>(p, in, ld_in, out, ld_out, nrhs);
+    // threads per group: Nout rounded up to a power of 2 (at most 128); groups per
+    // block: as many as fill 128 threads within 48 KB of staging
+    int tpg = 1;
+    while (tpg < p.Nout && tpg < 128) tpg <<= 1;
+    const size_t per = (size_t)(p.Kin + (p.out_planar ? p.Nout : 0)) * NT * sizeof(float2);
+    const int gpb = (int)std::max<size_t>(1, std::min<size_t>(128 / tpg, 49152 / per));
+    const int threads = gpb > 1 ? gpb * tpg : std::min(128, (p.Nout + 31) / 32 * 32);
+    if (gpb == 1) tpg = threads;
+    const long long ngroups = (long long)p.nA * p.nB;
+    const long long blocks = (ngroups + gpb - 1) / gpb * ntiles;
+    bfq::quad_pass_kernel<NT><<<(unsigned)blocks, threads, per * gpb, s>>>(p, in, ld_in, out, ld_out, nrhs, gpb, tpg);
     return cudaGetLastError();
 }
 
 cudaError_t run_pass(const bfq::Pass &p, const float2 *in, long long ld_in, float2 *out, long long ld_out, int nrhs,
                      cudaStream_t s) {
-    if (nrhs >= 32) return launch_pass<32>(p, in, ld_in, out, ld_out, nrhs, s);
-    if (nrhs >= 16) return launch_pass<16>(p, in, ld_in, out, ld_out, nrhs, s);
+    // a small stack (few outputs) gets a narrower RHS tile, so that 128 threads'
+    // worth of its groups fit 48 KB of staging
+    int tpg = 1;
+    while (tpg < p.Nout && tpg < 128) tpg <<= 1;
+    const long long fit = 49152 / ((long long)(p.Kin + p.Nout) * 8 * (128 / tpg));
+    const int cap = fit >= 32 ? 32 : fit >= 16 ? 16 : fit >= 8 ? 8 : 32;   // (below 8: one group per block)
+    if (nrhs >= 32 && cap >= 32) return launch_pass<32>(p, in, ld_in, out, ld_out, nrhs, s);
+    if (nrhs >= 16 && cap >= 16) return launch_pass<16>(p, in, ld_in, out, ld_out, nrhs, s);
     if (nrhs >= 8) return launch_pass<8>(p, in, ld_in, out, ld_out, nrhs, s);
     if (nrhs >= 4) return launch_pass<4>(p, in, ld_in, out, ld_out, nrhs, s);
     if (nrhs >= 2) return launch_pass<2>(p, in, ld_in, out, ld_out, nrhs, s);
@@ -411,7 +462,7 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&Q->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(1, std::atoi(e));
+    if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(8, std::atoi(e));   // planar tiles need NT >= 8
     Q->tc = Q->nrhs_max >= Q->tc_min;
     if (Q->tc && bfint::tc_prepare() != cudaSuccess) {
         delete Q;
