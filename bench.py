@@ -345,7 +345,7 @@ def fp32_fma_peak_tflops(dev) -> float:
     return sms * 128 * 2 * 2.070e9 / 1e12
 
 
-def quad_line(dev, stream):
+def quad_line(dev, stream, name="fio2d_n65536_r24"):
     """The 2D workload: a 256 x 256 grid (N = 65536), quadtrees of depth 8 with
     one point per leaf, rank 24 (level ranks 24, 24, 16, 4, 1), seeded
     synthetic factor values; apply + adjoint of 1 vector (CUDA-core level
@@ -358,13 +358,14 @@ def quad_line(dev, stream):
     from paper_1502_01379_gb300 import capi
     from bfinputs import complex_normal
     from bfinputs.quad import QUAD_CONFIGS, quad_sizes, synthetic_quad_factors
-    cfg = QUAD_CONFIGS["fio2d_n65536_r24"]
+    cfg = QUAD_CONFIGS[name]
     L, n0, r, nr = cfg["L"], cfg["n0"], cfg["r"], cfg["nrhs"]
     F = synthetic_quad_factors(L, n0, r, seed=0, dtype=np.complex64)
     entries = F.nentries() - F.S.size            # complex entries of the dense group blocks (S folded in)
     plan = capi.bf_quad_create(F, nrhs_max=nr)
-    res = {"workload": "2D: butterfly factorization on quadtrees of a 2D-FIO-shaped N=65536 matrix (256x256 grid), "
-                       "L=8, leaf=1, r=24, seeded synthetic factor values; step = apply + adjoint",
+    res = {"workload": f"{name}: 2D butterfly factorization on quadtrees of a 2D-FIO-shaped N={n0 << (2 * L)} matrix "
+                       f"({1 << (L + (n0.bit_length() - 1) // 2)}^2 grid), L={L}, leaf={n0}, r={r}, seeded synthetic "
+                       "factor values; step = apply + adjoint",
            "factor_entries": int(entries), "plan_device_gb": capi.bf_quad_device_bytes(plan) / 1e9,
            "launches_per_apply": capi.bf_quad_passes(plan), "tensor_core_levels": capi.bf_quad_tc_passes(plan)}
     peak, peak_src = load_peaks()
@@ -394,7 +395,7 @@ def quad_line(dev, stream):
                      "roofline": {"bound": "hbm", "achieved": alg / (ms / 2 / 1e3) / 1e9, "peak": peak,
                                   "unit": "GB/s", "frac": alg / (ms / 2 / 1e3) / 1e9 / peak, "peak_source": peak_src,
                                   "bytes_note": "per apply: every dense group block once (complex64) + in/out vectors"}}
-    # 128 vectors: inner levels on the tensor cores, every rung
+    # nr (>= 32) vectors: inner levels on the tensor cores, every rung
     g = torch.from_numpy(complex_normal((nr, F.N), seed=40 + nr, dtype=np.complex64)).to(dev)
     u, v = torch.empty_like(g), torch.empty_like(g)
     plain = torch.empty_like(g)
@@ -407,7 +408,7 @@ def quad_line(dev, stream):
     tc_mac = 0
     for lv in range(L // 2, L - 1):
         for kin, nout in ((4 * rk[lv + 1], 4 * rk[lv]), (4 * rk[lv], 4 * rk[lv + 1])):
-            tc_mac += (s["nblocks"] // 4) * (2 * nout) * kin * 128 * 2
+            tc_mac += (s["nblocks"] // 4) * (2 * nout) * kin * 128 * 2 * ((nr + 127) // 128)
     useful = 8.0 * entries * nr
     tf32_peak, tf32_src = tf32_peak_tflops()
     rungs = {}
@@ -431,7 +432,7 @@ def quad_line(dev, stream):
                                        "(the two CUDA-core edge levels included in the time)"}
         rungs[name] = ent
     capi.bf_quad_set_precision(plan, capi.BF_PREC_FP32)
-    res["nrhs_128"] = rungs
+    res[f"nrhs_{nr}"] = rungs
     plan.destroy()
     return res
 
@@ -689,7 +690,17 @@ def main(argv=None):
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl")
-    out = run_ours(args, rank, world, local)
+    from bfinputs.quad import QUAD_CONFIGS
+    if args.workload in QUAD_CONFIGS:
+        # a 2D workload alone (the 256 x 256 one is also a line of the default run), e.g. for profiling
+        import torch
+        from paper_1502_01379_gb300 import build as pkg_build
+        pkg_build.build()
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        out = {"workload": args.workload, "quad2d": quad_line(dev, torch.cuda.current_stream(dev), args.workload)}
+    else:
+        out = run_ours(args, rank, world, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -134,4 +134,7 @@ def synthetic_quad_factors(L: int, n0: int, r: int, seed: int = 0, dtype=np.comp
 # 128 RHS.
 QUAD_CONFIGS = {
     "fio2d_n65536_r24": {"L": 8, "n0": 1, "r": 24, "nrhs": 128},
+    # a small case of the same level shapes (96 x 96 groups) for profiling: 128 x 128
+    # grid, depth 6, four points per leaf, 256 vectors (level vectors of ~200 MB)
+    "fio2d_n16384_r24": {"L": 6, "n0": 4, "r": 24, "nrhs": 256},
 }

@@ -675,7 +675,10 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
             p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs) ? 1 : 0;
         const long long items = ntiles * P.m * wp.ngroups;
         const int grid = (int)std::min<long long>(items, P.num_sms);
-        bftc::bf_tc_kernel<<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+        if (p.bf16)
+            bftc::bf_tc_kernel<true><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+        else
+            bftc::bf_tc_kernel<false><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
         if (tm && ps + 1 < np && !D.pass[ps + 1].down && wp.down) cudaEventRecord(tm->b, s);
     }
     if (tm) cudaEventRecord(tm->c, s);
@@ -1071,8 +1074,7 @@ bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, c
         const bool fits = (1 << std::min(c.kmax, std::max(P->h, 0))) * std::max(n0, r) <= bftc::kMaxDim;
         if (fits && set_tc_dims(P->tfwd, *P) && set_tc_dims(P->tadj, *P)) {
             P->tc = true;
-            if (cudaFuncSetAttribute(bftc::bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)bftc::kSmemBytes) != cudaSuccess)
+            if (bfint::tc_prepare() != cudaSuccess)
                 return fail(cuda_fail(cudaErrorInvalidValue));
         } else {
             P->tfwd.pass.clear();
@@ -1473,7 +1475,11 @@ bf_status bf_batch_destroy(bf_batch B) {
 namespace bfint {
 
 cudaError_t tc_prepare() {
-    return cudaFuncSetAttribute(bftc::bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bftc::kSmemBytes);
+    const cudaError_t e = cudaFuncSetAttribute(bftc::bf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bftc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(bftc::bf_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bftc::kSmemBytes);
 }
 
 cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
@@ -1509,7 +1515,10 @@ cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
     const long long ntiles = (q.nrhs + bftc::NR - 1) / bftc::NR;
     const long long items = (long long)q.ngroups * q.parts * ntiles;
     const int grid = (int)std::min<long long>(items, num_sms);
-    bftc::bf_tc_kernel<<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+    if (p.bf16)
+            bftc::bf_tc_kernel<true><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+        else
+            bftc::bf_tc_kernel<false><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
     return cudaGetLastError();
 }
 

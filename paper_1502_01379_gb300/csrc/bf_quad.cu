@@ -185,6 +185,7 @@ struct bf_quad_s {
     bool tc = false;          // tensor-core passes built (nrhs_max >= 32)
     int tc_min = 32;          // smallest chunk of vectors the tensor-core path serves
     int tc_split = 3, tc_bf16 = 0;
+    int kc_max = 32;          // tensor-core K-chunk limit (BF_QUAD_KC: 32 or 64)
     unsigned *d_err = nullptr;
 };
 
@@ -276,7 +277,14 @@ bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::
                 each = D / n;
                 return D % n == 0 && each % 16 == 0;
             };
-            hp.tc = Q.tc && !edge && split64(p.Kin, hp.chunks, hp.Kc) && split64(p.Nout, hp.parts, hp.Nc);
+            // K-chunks of at most Q.kc_max (32: two tiles fit the staging area, so the
+            // next tile's copy overlaps this one's conversion), else of at most 64
+            auto split_k = [&](int D, int &n, int &each) {
+                for (n = 1; n <= D / 16; ++n)
+                    if (D % n == 0 && (each = D / n) <= Q.kc_max && each % 16 == 0) return true;
+                return split64(D, n, each);
+            };
+            hp.tc = Q.tc && !edge && split_k(p.Kin, hp.chunks, hp.Kc) && split64(p.Nout, hp.parts, hp.Nc);
             const size_t tper = (size_t)2 * hp.Nc * hp.Kc;   // floats per (group, part, chunk) block
             std::vector<float> tch;
             if (hp.tc) {
@@ -464,6 +472,7 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
     cudaDeviceGetAttribute(&Q->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(8, std::atoi(e));   // planar tiles need NT >= 8
     Q->tc = Q->nrhs_max >= Q->tc_min;
+    if (const char *e = std::getenv("BF_QUAD_KC")) Q->kc_max = std::atoi(e) >= 64 ? 64 : 32;
     if (Q->tc && bfint::tc_prepare() != cudaSuccess) {
         delete Q;
         return qfail(cudaErrorUnknown);

@@ -254,7 +254,7 @@ struct Smem {
     unsigned char *xs;                 // input staging
     float4 *tr;                        // per-warp transpose tiles (output rows)
     uint64_t *full, *empty, *bready;   // [kStages]
-    uint64_t *xfull, *xfree;           // staging landed / consumed
+    uint64_t *xfull, *xfree;           // [2]: staging buffer landed / consumed
     uint64_t *xrready, *xiready;       // Re X / Im X written (and D / E of the last item read)
     uint64_t *ddone, *edone;           // D group / E group of MMAs completed
     uint32_t *tmem_slot;
@@ -304,6 +304,13 @@ __device__ __forceinline__ Item decode(const TcParams &p, int item, int chunk, i
     }
     it.nt = min(NR, p.nrhs - it.t * NR);
     return it;
+}
+// Input staging buffers: two halves of the staging area when an item's tile
+// fits one (2D levels with K-chunks of at most 32 positions), so the next
+// tile's copy overlaps this tile's conversion; else one.
+constexpr uint32_t kHalfStage = kStageBytes / 2;
+__device__ __forceinline__ int nbufs(const TcParams &p) {
+    return (p.load_kind == LD_QUAD && (uint32_t)p.Kin * NR * 8u <= kHalfStage) ? 2 : 1;
 }
 // LD_QUAD / ST_QUAD: first input / output block index of the item's group.
 __device__ __forceinline__ long long quad_in_base(const TcParams &p, const Item &w) {
@@ -393,17 +400,20 @@ __device__ __forceinline__ const uint16_t *block_src16(const TcParams &p, const 
     return p.fac16 + w.blk * (2ll * p.Nout * p.Kin) * bf16_parts(p);
 }
 // Bytes of one item's block as streamed: FP32, or the BF16 parts.
+template <bool BF>
 __device__ __forceinline__ uint32_t block_bytes(const TcParams &p) {
-    return p.bf16 ? part_bytes(p) * (uint32_t)bf16_parts(p) : 2u * p.Nout * p.Kin * 4u;
+    return BF ? part_bytes(p) * (uint32_t)bf16_parts(p) : 2u * p.Nout * p.Kin * 4u;
 }
 
 // Producer warp: the item's block F into ring slot (it % kStages), then its
 // input tile into the staging buffer once the epilogue warps have converted
 // the previous one; with the copies of item i, L2 prefetches of item i+1.
+template <bool BF>
 __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int ntiles, int nitems) {
     const int lane = threadIdx.x & 31;
-    const uint32_t ubytes = block_bytes(p);
+    const uint32_t ubytes = block_bytes<BF>(p);
     uint32_t nf = 0, nx = 0;   // factor copies / staging groups issued
+    const uint32_t nb = (uint32_t)nbufs(p);
     for (int sub = 0; sub_item(p, sub) < nitems; ++sub) {
         const Item w = decode(p, sub_item(p, sub), sub % nchunks(p), ntiles);
         const uint32_t slot = nf % kStages, use = nf / kStages;
@@ -412,7 +422,7 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
             ok = !*s.abort_flag && (use == 0 || bfk::mbar_wait(&s.empty[slot], (use - 1) & 1, s.abort_flag, p.err));
             if (ok) {
                 bfk::mbar_arrive_expect_tx(&s.full[slot], ubytes);
-                if (!p.bf16) {
+                if (!BF) {
                     bfk::bulk_g2s(s.ring + (size_t)slot * (kSlotBytes / 4), block_src(p, w), ubytes, &s.full[slot]);
                 } else {   // parts 0, 1 into the ring slot, part 2 (three-way split) into the second buffer
                     const uint32_t pb = part_bytes(p), n01 = min(ubytes, 2u * pb);
@@ -426,18 +436,20 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
         }
         if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0) == 0) break;
         ++nf;
-        if (nx > 0 && !warp_wait(s.xfree, (nx - 1) & 1, s.abort_flag, p.err)) break;
-        if (lane == 0) bfk::mbar_arrive_expect_tx(s.xfull, tile_bytes(p, w));
+        const uint32_t xb = nx % nb, xuse = nx / nb;
+        if (xuse > 0 && !warp_wait(&s.xfree[xb], (xuse - 1) & 1, s.abort_flag, p.err)) break;
+        if (lane == 0) bfk::mbar_arrive_expect_tx(&s.xfull[xb], tile_bytes(p, w));
         __syncwarp();
+        unsigned char *xs = s.xs + xb * kHalfStage;
         if (p.load_kind == LD_POINTS && p.use_tmap) {
             if (lane < p.Kin / 16)
-                tma_load_2d(s.xs + (size_t)lane * kBoxBytes, &p.tmap, points_x(p, w) + 32 * lane, w.t * NR, s.xfull);
+                tma_load_2d(xs + (size_t)lane * kBoxBytes, &p.tmap, points_x(p, w) + 32 * lane, w.t * NR, &s.xfull[xb]);
         } else
-            tile_copies(p, w, lane, [&](uint32_t off, const void *src, uint32_t b) { bfk::bulk_g2s(s.xs + off, src, b, s.xfull); });
+            tile_copies(p, w, lane, [&](uint32_t off, const void *src, uint32_t b) { bfk::bulk_g2s(xs + off, src, b, &s.xfull[xb]); });
         ++nx;
         if (sub_item(p, sub + 1) < nitems) {   // next item of this CTA: into L2
             const Item w2 = decode(p, sub_item(p, sub + 1), (sub + 1) % nchunks(p), ntiles);
-            if (lane == 0) prefetch_l2(p.bf16 ? (const void *)block_src16(p, w2) : (const void *)block_src(p, w2), ubytes);
+            if (lane == 0) prefetch_l2(BF ? (const void *)block_src16(p, w2) : (const void *)block_src(p, w2), ubytes);
             if (p.load_kind == LD_POINTS && p.use_tmap) {
                 if (lane < p.Kin / 16) prefetch_tile_2d(&p.tmap, points_x(p, w2) + 32 * lane, w2.t * NR);
             } else {
@@ -449,12 +461,13 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
     if (lane == 0) {
         for (uint32_t k = nf > (uint32_t)kStages ? nf - kStages : 0; k < nf; ++k)
             drain_wait(&s.full[k % kStages], (k / kStages) & 1);
-        if (nx > 0) drain_wait(s.xfull, (nx - 1) & 1);
+        for (uint32_t k = nx > nb ? nx - nb : 0; k < nx; ++k) drain_wait(&s.xfull[k % nb], (k / nb) & 1);
     }
 }
 
 // Prep warp: each streamed block rounded to TF32 in place and its low part
 // F_lo, in the same operand layout.
+template <bool BF>
 __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitems) {
     const int lane = threadIdx.x & 31;
     const int n4 = 2 * p.Nout * p.Kin / 4;
@@ -462,7 +475,7 @@ __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitem
     for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
         const uint32_t slot = it % kStages;
         const bool ok = warp_wait(&s.full[slot], (it / kStages) & 1, s.abort_flag, p.err);
-        if (ok && !p.bf16) {   // (BF16 rungs stream blocks already split: nothing to do)
+        if (ok && !BF) {   // (BF16 rungs stream blocks already split: nothing to do)
             // the block rounded to TF32 in place (the MMAs read it), F_lo = F - round(F)
             float4 *hi = reinterpret_cast<float4 *>(s.ring + (size_t)slot * (kSlotBytes / 4));
             float4 *lo = reinterpret_cast<float4 *>(s.blo + (size_t)slot * (kSlotBytes / 4));
@@ -479,6 +492,7 @@ __device__ __forceinline__ void prep(const TcParams &p, const Smem &s, int nitem
 }
 
 // MMA warp (one thread): per item the D group (Re X) then the E group (Im X).
+template <bool BF>
 __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uint32_t tmem, int nitems) {
     const int rows = 2 * p.Nout;
     const uint32_t lbo = (uint32_t)(rows >> 3) * 128u;
@@ -499,7 +513,7 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
             }
             const uint32_t d = tmem + (grp ? kE : kD);
             const uint32_t xh = tmem + (grp ? kXi : kXr), xl = tmem + (grp ? kXil : kXrl);
-            if (ok && p.bf16 && p.split == 6) {
+            if (BF && ok && p.split == 6) {
                 // BF16 three-way split: the terms of order 2^-16 (hi lo, lo hi, mid mid),
                 // then 2^-8 (hi mid, mid hi), then hi hi.  X_mid sits 32 columns after X_hi.
                 const uint32_t pb = 2u * p.Nout * p.Kin * 2u;
@@ -518,7 +532,7 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
                 }
                 for (int kk = 0; kk < nk; ++kk)
                     mma_ts_bf16(d, xh + (uint32_t)(8 * kk), sdesc(bhi + (uint32_t)(2 * kk) * lbo, lbo, 128), idesc16, 1);
-            } else if (ok && p.bf16) {
+            } else if (BF && ok) {
                 // BF16: K = 16 per MMA; F_hi, F_lo consecutive in the ring slot
                 const uint32_t idesc16 = idesc_bf16(rows), bhi = b1, blow = b1 + 2u * p.Nout * p.Kin * 2u;
                 bool first = true;
@@ -566,14 +580,16 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
 
 // One part (0 = real, 1 = imaginary) of the staged input tile -> X and X_lo
 // in tensor memory (this thread's RHS lane, positions of its half).
-__device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32_t lb, int mlane, int hf, int part) {
+template <bool BF>
+__device__ __forceinline__ void convert(const TcParams &p, const unsigned char *xs, uint32_t lb, int mlane, int hf,
+                                        int part) {
     const int half = p.Kin >> 1;
     const uint32_t ch = part ? kXi : kXr, cl = part ? kXil : kXrl;
     for (int e = hf * half; e < (hf + 1) * half; e += 8) {
         float v[8], vl[8];
         if (p.load_kind == LD_POINTS && p.use_tmap) {
             // tile e/16, row mlane (128 B), 16-byte chunk c stored at c ^ (mlane % 8)
-            const unsigned char *row = s.xs + (size_t)(e >> 4) * kBoxBytes + (size_t)mlane * 128;
+            const unsigned char *row = xs + (size_t)(e >> 4) * kBoxBytes + (size_t)mlane * 128;
             const int c0 = (e & 15) >> 1;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -582,7 +598,7 @@ __device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32
                 v[2 * i + 1] = part ? q.w : q.z;
             }
         } else if (p.load_kind == LD_POINTS) {
-            const float4 *row = reinterpret_cast<const float4 *>(s.xs + (size_t)mlane * kPointRow) + (e >> 1);
+            const float4 *row = reinterpret_cast<const float4 *>(xs + (size_t)mlane * kPointRow) + (e >> 1);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float4 q = row[i];
@@ -590,11 +606,11 @@ __device__ __forceinline__ void convert(const TcParams &p, const Smem &s, uint32
                 v[2 * i + 1] = part ? q.w : q.z;
             }
         } else {
-            const float *col = reinterpret_cast<const float *>(s.xs) + (size_t)e * 2 * NR + part * NR + mlane;
+            const float *col = reinterpret_cast<const float *>(xs) + (size_t)e * 2 * NR + part * NR + mlane;
 #pragma unroll
             for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * 2 * NR];
         }
-        if (p.bf16) {   // BF16 pairs: element e + 2i in the low half of column (e / 2) + i
+        if (BF) {   // BF16 pairs: element e + 2i in the low half of column (e / 2) + i
             uint32_t h[4], m[4], l[4];
             if (p.split == 6) {
                 split3_bf16x8(v, h, m, l);
@@ -739,6 +755,8 @@ __global__ void bf16_split_kernel(const float *fac, uint4 *out, long long nblock
     }
 }
 
+// BF: the BF16 rungs (p.bf16 = 1) or the TF32 rungs, one instantiation each.
+template <bool BF>
 __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem s;
@@ -751,12 +769,12 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
     s.empty = bars + kStages;
     s.bready = bars + 2 * kStages;
     s.xfull = bars + 3 * kStages;
-    s.xfree = s.xfull + 1;
-    s.xrready = s.xfull + 2;
-    s.xiready = s.xfull + 3;
-    s.ddone = s.xfull + 4;
-    s.edone = s.xfull + 5;
-    s.tmem_slot = reinterpret_cast<uint32_t *>(s.xfull + 6);
+    s.xfree = s.xfull + 2;
+    s.xrready = s.xfull + 4;
+    s.xiready = s.xfull + 5;
+    s.ddone = s.xfull + 6;
+    s.edone = s.xfull + 7;
+    s.tmem_slot = reinterpret_cast<uint32_t *>(s.xfull + 8);
     s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
@@ -765,8 +783,10 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
             bfk::mbar_init(&s.empty[i], 1);
             bfk::mbar_init(&s.bready[i], 1);
         }
-        bfk::mbar_init(s.xfull, 1);
-        bfk::mbar_init(s.xfree, kEpiWarps);
+        for (int b = 0; b < 2; ++b) {
+            bfk::mbar_init(&s.xfull[b], 1);
+            bfk::mbar_init(&s.xfree[b], kEpiWarps);
+        }
         bfk::mbar_init(s.xrready, kEpiWarps);
         bfk::mbar_init(s.xiready, kEpiWarps);
         bfk::mbar_init(s.ddone, 1);
@@ -788,15 +808,16 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
     const int ntiles = (p.nrhs + NR - 1) / NR;
     const int nitems = nwork(p, ntiles);
     if (warp == kProdWarp) {
-        producer(p, s, ntiles, nitems);
+        producer<BF>(p, s, ntiles, nitems);
     } else if (warp == kPrepWarp) {
-        prep(p, s, nitems);
+        prep<BF>(p, s, nitems);
     } else if (warp == kMmaWarp) {
-        if ((tid & 31) == 0) mma_issuer(p, s, tmem, nitems);
+        if ((tid & 31) == 0) mma_issuer<BF>(p, s, tmem, nitems);
     } else {
         const int q = warp & 3, hf = warp >> 2;
         const int mlane = q * 32 + (tid & 31);
         const uint32_t lb = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t nb = (uint32_t)nbufs(p);
         uint32_t it = 0;
         Item prev{};
         Acc acc;
@@ -808,8 +829,10 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
                 tc_fence_after();
                 if (okd && prev.last) read_d(p, lb, hf, acc);
             }
-            const bool okx = warp_wait(s.xfull, it & 1, s.abort_flag, p.err);
-            if (okx) convert(p, s, lb, mlane, hf, 0);
+            const uint32_t xb = it % nb;
+            const unsigned char *xs = s.xs + xb * kHalfStage;
+            const bool okx = warp_wait(&s.xfull[xb], (it / nb) & 1, s.abort_flag, p.err);
+            if (okx) convert<BF>(p, xs, lb, mlane, hf, 0);
             tc_fence_before();
             warp_arrive(s.xrready);
             if (it > 0) {   // item it-1: E, combine, store (item it's D group is running)
@@ -817,10 +840,10 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
                 tc_fence_after();
                 if (okd && oke && prev.last) finish(p, s, prev, lb, q, mlane, hf, acc);
             }
-            if (okx) convert(p, s, lb, mlane, hf, 1);
+            if (okx) convert<BF>(p, xs, lb, mlane, hf, 1);
             tc_fence_before();
             warp_arrive(s.xiready);
-            warp_arrive(s.xfree);
+            warp_arrive(&s.xfree[xb]);
             prev = w;
         }
         if (it > 0) {
