@@ -61,10 +61,39 @@ __device__ __forceinline__ long long planar_at(long long R, long long j, long lo
     return ((j >> 7) * R + pos) * 256 + (j & 127);
 }
 
-// One vector at a time the kernel streams the factors: 32 registers keep 16
-// blocks of 128 threads (2048 threads) resident for enough loads in flight.
+// One vector at a time: a stream over the blocks, one group per thread block
+// (as many thread blocks in flight as the SM holds), one output row per thread.
+__global__ void __launch_bounds__(128) quad_gemv_kernel(const Pass p, const float2 *__restrict__ in,
+                                                        float2 *__restrict__ out) {
+    extern __shared__ float2 xs[];   // [Kin]
+    const long long g = blockIdx.x;
+    const int A = (int)(g / p.nB), B = (int)(g - (long long)A * p.nB);
+    const long long in_base = p.ain * A + p.bin * B;
+    for (int k = threadIdx.x; k < p.Kin; k += blockDim.x) {
+        const int c = k / p.bsz_in, x = k - c * p.bsz_in;
+        xs[k] = in[(in_base + c * p.sin) * p.bsz_in + x];
+    }
+    __syncthreads();
+    const long long out_base = p.aout * A + p.bout * B;
+    const float2 *Fg = p.F + g * (long long)p.Kin * p.Nout;
+    for (int o = threadIdx.x; o < p.Nout; o += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        const float2 *f = Fg + o;
+#pragma unroll 4
+        for (int k = 0; k < p.Kin; ++k) {
+            const float2 fv = __ldg(f + (long long)k * p.Nout);
+            const float2 xv = xs[k];
+            acc.x = fmaf(fv.x, xv.x, fmaf(-fv.y, xv.y, acc.x));
+            acc.y = fmaf(fv.x, xv.y, fmaf(fv.y, xv.x, acc.y));
+        }
+        const int c = o / p.bsz_out, x = o - c * p.bsz_out;
+        out[(out_base + c * p.sout) * p.bsz_out + x] = acc;
+    }
+}
+
+// NT vectors per thread block (2..32), RHS-major or planar tiles.
 template <int NT>
-__global__ void __launch_bounds__(128, NT == 1 ? 16 : 1) quad_pass_kernel(const Pass p, const float2 *__restrict__ in, long long ld_in,
+__global__ void __launch_bounds__(128) quad_pass_kernel(const Pass p, const float2 *__restrict__ in, long long ld_in,
                                                         float2 *__restrict__ out, long long ld_out, int nrhs, int gpb,
                                                         int tpg) {
     // gpb consecutive groups per thread block, tpg threads per group (small stacks
@@ -185,7 +214,7 @@ struct bf_quad_s {
     bool tc = false;          // tensor-core passes built (nrhs_max >= 32)
     int tc_min = 32;          // smallest chunk of vectors the tensor-core path serves
     int tc_split = 3, tc_bf16 = 0;
-    int kc_max = 32;          // tensor-core K-chunk limit (BF_QUAD_KC: 32 or 64)
+    int kc_max = 64;          // tensor-core K-chunk limit (BF_QUAD_KC: 32 or 64)
     unsigned *d_err = nullptr;
 };
 
@@ -277,8 +306,11 @@ bf_status build_direction(bf_quad_s &Q, const bf_factors &f, bool adjoint, std::
                 each = D / n;
                 return D % n == 0 && each % 16 == 0;
             };
-            // K-chunks of at most Q.kc_max (32: two tiles fit the staging area, so the
-            // next tile's copy overlaps this one's conversion), else of at most 64
+            // K-chunks of at most Q.kc_max.  Chunks of at most 32 positions get two
+            // staging buffers (the next tile's copy overlaps this one's conversion),
+            // but splitting a 96-wide stack into three of them instead of two of 48
+            // measured slower (9.1 vs 7.7 ms per 128-vector apply at 256 x 256), so
+            // the default is 64.
             auto split_k = [&](int D, int &n, int &each) {
                 for (n = 1; n <= D / 16; ++n)
                     if (D % n == 0 && (each = D / n) <= Q.kc_max && each % 16 == 0) return true;
@@ -416,6 +448,13 @@ cudaError_t launch_pass(const bfq::Pass &p, const float2 *in, long long ld_in, f
     return cudaGetLastError();
 }
 
+cudaError_t run_gemv(const bfq::Pass &p, const float2 *in, float2 *out, cudaStream_t s) {
+    const int threads = std::min(128, (p.Nout + 31) / 32 * 32);
+    bfq::quad_gemv_kernel<<<(unsigned)((long long)p.nA * p.nB), threads, (size_t)p.Kin * sizeof(float2), s>>>(p, in,
+                                                                                                           out);
+    return cudaGetLastError();
+}
+
 cudaError_t run_pass(const bfq::Pass &p, const float2 *in, long long ld_in, float2 *out, long long ld_out, int nrhs,
                      cudaStream_t s) {
     // a small stack (few outputs) gets a narrower RHS tile, so that 128 threads'
@@ -429,6 +468,9 @@ cudaError_t run_pass(const bfq::Pass &p, const float2 *in, long long ld_in, floa
     if (nrhs >= 8) return launch_pass<8>(p, in, ld_in, out, ld_out, nrhs, s);
     if (nrhs >= 4) return launch_pass<4>(p, in, ld_in, out, ld_out, nrhs, s);
     if (nrhs >= 2) return launch_pass<2>(p, in, ld_in, out, ld_out, nrhs, s);
+    // one vector: the streaming kernel (0.71 ms per apply at 256 x 256 against 0.90 for
+    // the tiled kernel with one-vector tiles)
+    if (!p.in_planar && !p.out_planar) return run_gemv(p, in, out, s);
     return launch_pass<1>(p, in, ld_in, out, ld_out, nrhs, s);
 }
 
@@ -472,7 +514,7 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
     cudaDeviceGetAttribute(&Q->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(8, std::atoi(e));   // planar tiles need NT >= 8
     Q->tc = Q->nrhs_max >= Q->tc_min;
-    if (const char *e = std::getenv("BF_QUAD_KC")) Q->kc_max = std::atoi(e) >= 64 ? 64 : 32;
+    if (const char *e = std::getenv("BF_QUAD_KC")) Q->kc_max = std::atoi(e) <= 32 ? 32 : 64;
     if (Q->tc && bfint::tc_prepare() != cudaSuccess) {
         delete Q;
         return qfail(cudaErrorUnknown);
