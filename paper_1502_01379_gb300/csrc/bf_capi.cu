@@ -671,6 +671,7 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
         p.nrhs = nrhs;
         p.split = P.tc_split;
         p.bf16 = P.tc_bf16;
+        p.stall = P.inject_stall;
         if (p.load_kind == bftc::LD_POINTS && env_int("BF_TC_TMAP", 1) == 1)
             p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs) ? 1 : 0;
         const long long items = ntiles * P.m * wp.ngroups;
@@ -1500,6 +1501,7 @@ cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
     p.nrhs = q.nrhs;
     p.split = q.split;
     p.bf16 = q.bf16;
+    p.stall = q.stall;
     p.q_ain = q.ain;
     p.q_bin = q.bin;
     p.q_sin = q.sin;

@@ -23,6 +23,7 @@ struct QuadTc {
     long long ain, bin, sin, aout, bout, sout;
     int bszi, bszo, nB, ngroups, parts, chunks, Kin, Nout, nrhs;
     int split, bf16;         // as bf_plan_set_precision's rungs
+    int stall;               // failure-detection test hook (no copies: every wait expires)
 };
 
 // Sets the tensor-core kernel's shared-memory attribute (once per plan).

@@ -215,6 +215,7 @@ struct bf_quad_s {
     int tc_min = 32;          // smallest chunk of vectors the tensor-core path serves
     int tc_split = 3, tc_bf16 = 0;
     int kc_max = 64;          // tensor-core K-chunk limit (BF_QUAD_KC: 32 or 64)
+    int inject_stall = 0;     // failure-detection test hook (BF_INJECT_STALL=1 at creation)
     unsigned *d_err = nullptr;
 };
 
@@ -515,6 +516,7 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
     if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(8, std::atoi(e));   // planar tiles need NT >= 8
     Q->tc = Q->nrhs_max >= Q->tc_min;
     if (const char *e = std::getenv("BF_QUAD_KC")) Q->kc_max = std::atoi(e) <= 32 ? 32 : 64;
+    if (const char *e = std::getenv("BF_INJECT_STALL")) Q->inject_stall = std::atoi(e) == 1 ? 1 : 0;
     if (Q->tc && bfint::tc_prepare() != cudaSuccess) {
         delete Q;
         return qfail(cudaErrorUnknown);
@@ -584,6 +586,7 @@ bf_status bf_quad_apply(bf_quad Q, const void *in, void *out, int nrhs, long lon
                 q.ngroups = hp.p.nA * hp.p.nB;
                 q.parts = hp.parts, q.chunks = hp.chunks, q.Kin = hp.Kc, q.Nout = hp.Nc, q.nrhs = nc;
                 q.split = Q->tc_split, q.bf16 = Q->tc_bf16;
+                q.stall = Q->inject_stall;
                 e = bfint::quad_tc_launch(q, Q->num_sms, stream);
             } else {
                 bfq::Pass pp = hp.p;

@@ -114,6 +114,8 @@ struct alignas(64) TcParams {
     int Kin, Nout;
     int nrhs;
     int split;              // products per real product: 1 plain; 3 hi/lo split; 6 (BF16 only) hi/mid/lo split
+    int stall;              // failure-detection test hook: the producer issues no copies, so every
+                            // consumer wait runs into its bound and the launch reports BF_ERR_TIMEOUT
     int bf16;               // operand type: 0 TF32 (kind::tf32, K = 8), 1 BF16 (kind::f16, K = 16)
     int use_tmap;           // LD_POINTS: load the tile by tensor-map copies (else one copy per row)
     // LD_QUAD / ST_QUAD: one level of a 2D (quadtree) factorization.  Group g = A q_nB + B
@@ -414,7 +416,7 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
     const uint32_t ubytes = block_bytes<BF>(p);
     uint32_t nf = 0, nx = 0;   // factor copies / staging groups issued
     const uint32_t nb = (uint32_t)nbufs(p);
-    for (int sub = 0; sub_item(p, sub) < nitems; ++sub) {
+    for (int sub = 0; !p.stall && sub_item(p, sub) < nitems; ++sub) {
         const Item w = decode(p, sub_item(p, sub), sub % nchunks(p), ntiles);
         const uint32_t slot = nf % kStages, use = nf / kStages;
         bool ok = true;

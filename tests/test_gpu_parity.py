@@ -404,3 +404,28 @@ def test_bf16_rungs_keep_split_blocks_only_while_set(bf):
         capi.bf_plan_set_precision(plan, prec)
         assert np.array_equal(_run(bf, plan, g), out[prec])
     plan.destroy()
+
+
+def test_tensor_core_bounded_waits_report_timeout(bf, monkeypatch):
+    """Failure detection on the tensor-core core, without a GPU fault: with the
+    stall hook its producer issues no copies, every wait of the other warps
+    runs into its bound, the launch ends with the error word set (tensor
+    memory released), bf_plan_check reports BF_ERR_TIMEOUT, and a plan made
+    afterwards computes the right result on the same context."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(4, 16, 16, seed=31, dtype=np.complex64)
+    monkeypatch.setenv("BF_INJECT_STALL", "1")
+    stalled = bf.bf_plan_create(F, nrhs_max=128)
+    monkeypatch.delenv("BF_INJECT_STALL")
+    g = complex_normal((128, F.N), seed=32, dtype=np.complex64)
+    x = torch.from_numpy(g).cuda()
+    y = torch.empty_like(x)
+    bf.bf_apply(stalled, x, y)
+    torch.cuda.synchronize()
+    with pytest.raises(bf.BfError) as err:
+        bf.bf_plan_check(stalled)
+    assert err.value.status == bf.BF_ERR_TIMEOUT
+    stalled.destroy()
+    plan = bf.bf_plan_create(F, nrhs_max=128)
+    assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
+    plan.destroy()

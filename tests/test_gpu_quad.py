@@ -181,3 +181,28 @@ def test_quad_tensor_core_rungs(bf, L, n0, r, nrhs):
         torch.cuda.synchronize()
         assert _rel(tc, y.cpu().numpy()) < TOL
     plan.destroy()
+
+
+def test_quad_tensor_core_bounded_waits_report_timeout(bf, monkeypatch):
+    """The 2D tensor-core levels under the stall hook: every wait expires, the
+    launch returns, bf_quad_check reports BF_ERR_TIMEOUT (then clears it), and
+    a plan made afterwards is correct."""
+    from bfinputs import complex_normal
+    from bfinputs.quad import synthetic_quad_factors
+    from oracle import quad as Q
+    F = synthetic_quad_factors(4, 4, 16, seed=33, dtype=np.complex64)
+    monkeypatch.setenv("BF_INJECT_STALL", "1")
+    stalled = bf.bf_quad_create(F, nrhs_max=64)
+    monkeypatch.delenv("BF_INJECT_STALL")
+    assert bf.bf_quad_tc_passes(stalled) > 0
+    g = complex_normal((64, F.N), seed=34, dtype=np.complex64)
+    _gpu(bf, stalled, g)
+    with pytest.raises(bf.BfError) as err:
+        bf.bf_quad_check(stalled)
+    assert err.value.status == bf.BF_ERR_TIMEOUT
+    bf.bf_quad_check(stalled)
+    stalled.destroy()
+    plan = bf.bf_quad_create(F, nrhs_max=64)
+    assert _rel(_gpu(bf, plan, g), Q.bf_apply(F, g.T).T) < TOL
+    bf.bf_quad_check(plan)
+    plan.destroy()
