@@ -33,7 +33,7 @@ typedef enum {
     BF_ERR_INVALID = 1,      /* bad argument: null pointer, odd L, aliasing in/out, ld < N, ... */
     BF_ERR_CUDA = 2,         /* a CUDA runtime call failed (the CUDA error is cleared)          */
     BF_ERR_NOMEM = 3,        /* device or host allocation failed                               */
-    BF_ERR_UNSUPPORTED = 4,  /* valid but outside this build's limits (r > 32, n0 > 64, ...)   */
+    BF_ERR_UNSUPPORTED = 4,  /* valid but outside the library's compiled limits (r > 32, ...) */
     BF_ERR_TIMEOUT = 5,      /* a kernel's bounded wait expired; its output is not valid       */
 } bf_status;
 
@@ -42,7 +42,7 @@ typedef enum {
     BF_C128 = 2,             /* complex128: interleaved (re, im) double; S as double          */
 } bf_dtype;
 
-/* Shape of a factorization.  Limits of this build: L even, 0 <= L <= 24;
+/* Shape of a factorization.  Compiled limits: L even, 0 <= L <= 24;
  * 1 <= r <= 32; 1 <= leaf <= 64; and m * max(leaf, r) <= 8192 (one tree
  * node's vector segment must fit in shared memory). */
 typedef struct {

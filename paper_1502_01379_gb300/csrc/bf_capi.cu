@@ -1200,7 +1200,7 @@ const char *bf_status_string(bf_status s) {
         case BF_ERR_INVALID: return "BF_ERR_INVALID: invalid argument";
         case BF_ERR_CUDA: return "BF_ERR_CUDA: a CUDA runtime call failed";
         case BF_ERR_NOMEM: return "BF_ERR_NOMEM: out of memory";
-        case BF_ERR_UNSUPPORTED: return "BF_ERR_UNSUPPORTED: shape outside this build's limits";
+        case BF_ERR_UNSUPPORTED: return "BF_ERR_UNSUPPORTED: shape outside the library's compiled limits";
         case BF_ERR_TIMEOUT: return "BF_ERR_TIMEOUT: a kernel wait expired";
     }
     return "unknown bf_status";
