@@ -1,8 +1,9 @@
 """Pins of the 2D (quadtree) oracle against things other than itself: a
 hand-written Morton table, the 2D FFT, exactness when every block is kept at
 full rank, an independent sparse assembly of the factors, the adjoint
-identity, the dense product at the construction's accuracy, and the
-complementary low-rank property of the 2D FIO."""
+identity, the dense product at the construction's accuracy, the
+complementary low-rank property of the 2D FIO, and planted mistakes that the
+exactness pin must catch."""
 import numpy as np
 import pytest
 
@@ -112,3 +113,30 @@ def test_workload_shape_and_entry_count():
     assert s["ranks"] == {4: 24, 5: 24, 6: 16, 7: 4, 8: 1}
     transfer = sum(s["nblocks"] * s["ranks"][lv + 1] * 4 * s["ranks"][lv] for lv in range(4, 8))
     assert 2 * transfer == 538_968_064
+
+
+def test_exactness_pin_catches_planted_mistakes():
+    """Mistakes planted in the oracle's factors, each the effect of a plausible
+    slip in the 2D apply (M^h's blocks not transposed, a missing conjugate on
+    H^*, the children of a splitting level taken in the wrong order, a leaf
+    factor of the wrong leaf): every one breaks the full-rank exactness pin by
+    far more than its tolerance, so the pin would catch it."""
+    n, L, r = 8, 2, 16
+    F = Q.construct(n, L, r, "fio2", seed=21)
+    K = Q.entries(np.arange(n * n), np.arange(n * n), n)
+    g = complex_normal((n * n,), seed=22)
+    ref = K @ g
+    assert rel_err(Q.bf_apply(F, g), ref) < 1e-12
+
+    def broken(edit):
+        G = Q.QuadFactors(F.L, F.n0, F.r, F.VL.copy(), [a.copy() for a in F.H], F.S.copy(),
+                          [a.copy() for a in F.G], F.UL.copy(), dict(F.meta))
+        edit(G)
+        return rel_err(Q.bf_apply(G, g), ref)
+
+    assert broken(lambda G: G.S.__setitem__(slice(None), F.S.transpose(1, 0, 2))) > 1e-3
+    assert broken(lambda G: G.H.__setitem__(0, F.H[0].conj())) > 1e-3
+    nb = F.G[0].shape[0]
+    order = np.arange(nb).reshape(nb // 4, 4)[:, ::-1].reshape(-1)
+    assert broken(lambda G: G.G.__setitem__(0, F.G[0][order])) > 1e-3
+    assert broken(lambda G: G.UL.__setitem__(slice(None), F.UL[::-1])) > 1e-3
