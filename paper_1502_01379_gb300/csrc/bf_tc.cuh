@@ -700,12 +700,24 @@ __device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const I
             if (live) {
                 const long long base = quad_out_base(p, w);
                 float *dst = reinterpret_cast<float *>(p.out) + (long long)w.t * p.R * 2 * NR + mlane;
+                const int oo0 = w.part * p.Nout + o;
+                if ((p.q_bszo & 7) == 0) {   // the 8 outputs lie in one block: one index computation
+                    const int c = oo0 / p.q_bszo;
+                    const long long pos0 = (base + c * p.q_sout) * p.q_bszo + (oo0 - c * p.q_bszo);
+                    float *d0 = dst + pos0 * 2 * NR;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int oo = w.part * p.Nout + o + i, c = oo / p.q_bszo;
-                    const long long pos = (base + c * p.q_sout) * p.q_bszo + (oo - c * p.q_bszo);
-                    dst[pos * 2 * NR] = re[i];
-                    dst[pos * 2 * NR + NR] = im[i];
+                    for (int i = 0; i < 8; ++i) {
+                        d0[i * 2 * NR] = re[i];
+                        d0[i * 2 * NR + NR] = im[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int oo = oo0 + i, c = oo / p.q_bszo;
+                        const long long pos = (base + c * p.q_sout) * p.q_bszo + (oo - c * p.q_bszo);
+                        dst[pos * 2 * NR] = re[i];
+                        dst[pos * 2 * NR + NR] = im[i];
+                    }
                 }
             }
         } else if (live) {
