@@ -18,6 +18,10 @@ Modules (each function cites the passage of the paper it follows):
 * ``construct``-- the middle-level factorization (Sec. 3.1, Eq. KeqUMV) and
                   the recursive factorization of U^h and V^h (Sec. 3.2),
                   in the memory-saving row-node-at-a-time order (Sec. 3.3).
+* ``construct_mv`` -- the construction when only K g and K^* g are available
+                  (Sec. 3.1, first case): randomized SVDs of all middle blocks
+                  from 2 m (r + p) products (Sec. 2.1), then Sec. 3.2; and the
+                  composition K F K of Example 3 (Sec. 4).
 * ``apply``    -- the apply u = U^L G^{L-1}...G^h M^h (H^h)^*...(H^{L-1})^* (V^L)^* g
                   of Eq. (Kfactors) and its adjoint, one factor at a time.
 * ``grad``     -- reverse mode through the same chain: the gradient of a real
