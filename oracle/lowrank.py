@@ -15,7 +15,7 @@ Readings where the paper is silent:
 * A block with fewer than r rows or columns gives rank min(r, rows, cols);
   the factors are padded with zero columns to width r.
 * Random rows and columns are drawn uniformly without replacement; each draw
-  takes r*q indices (all of them if the block is smaller); the "few extra"
+  takes r*q indices (all of them if the block is smaller); the additional
   rows and columns of step 6 are also r*q each.
 """
 from __future__ import annotations
