@@ -6,9 +6,9 @@ check (the FP64 oracle and the CUDA library) receive their inputs from here.
 """
 from .factors import ButterflyFactors, tree_sizes
 from .workloads import (CONFIGS, BatchMember, Config, batched_workload, complex_normal, sample_rows,
-                        synthetic_factors)
+                        sketch_blocks, synthetic_factors)
 
 __all__ = [
     "ButterflyFactors", "tree_sizes", "CONFIGS", "Config", "complex_normal",
-    "synthetic_factors", "sample_rows", "BatchMember", "batched_workload",
+    "synthetic_factors", "sample_rows", "BatchMember", "batched_workload", "sketch_blocks",
 ]

@@ -102,6 +102,24 @@ def synthetic_factors(L: int, n0: int, r: int, seed: int = 0,
                             meta={"source": "synthetic", "seed": seed}).validate()
 
 
+def sketch_blocks(N: int, L: int, r: int, p: int = 5, seed: int = 0):
+    """The random Gaussian blocks of a construction from products (Sec. 3.1,
+    first case): C_jj and R_ii for the m = 2^{L/2} middle-level nodes, each
+    (N/m) x k complex standard normal with k = min(r + p, N/m), drawn from
+    streams keyed by (seed, side, node).  Returns (C, R) of shape (m, N/m, k)."""
+    m = 1 << (L // 2)
+    nb = N // m
+    k = min(r + p, nb)
+    out = []
+    for side in (0, 1):
+        blocks = np.empty((m, nb, k), dtype=np.complex128)
+        for j in range(m):
+            rng = _rng(seed, 77, side, j)
+            blocks[j] = (rng.standard_normal((nb, k)) + 1j * rng.standard_normal((nb, k))) / np.sqrt(2.0)
+        out.append(blocks)
+    return out[0], out[1]
+
+
 def sample_rows(N: int, count: int = 256, seed: int = 0) -> np.ndarray:
     """A sorted random set of ``count`` distinct rows (the set S of the
     accuracy measure epsilon^a in Sec. 4 has 256 points)."""

@@ -26,8 +26,8 @@ Readings where the paper is silent:
   products with vectors that depend on both i and j.)
 * p = 5, the oversampling the paper states (Sec. 2.1 and Sec. 4); when a block
   has fewer than r + p columns, r + p is capped at that size.
-* The Gaussian blocks are complex standard normal, drawn from streams keyed by
-  (seed, side, node); pivoted QR is LAPACK geqp3 (SciPy).
+* The Gaussian blocks are complex standard normal (``bfinputs.sketch_blocks``,
+  shared with the device construction); pivoted QR is LAPACK geqp3 (SciPy).
 
 Example 3 (Sec. 4): the composition K~ = K F K of the 1D FIO matrix K with the
 Fourier transform F between the space points x_j = j/N and the frequencies
@@ -40,16 +40,12 @@ import numpy as np
 import scipy.linalg as sla
 
 from bfinputs.factors import ButterflyFactors, tree_sizes
+from bfinputs.workloads import sketch_blocks
 
 from .construct import recursive_factorize
 from .lowrank import form_usv
 
 OVERSAMPLE = 5
-
-
-def _gaussian(seed: int, side: int, node: int, shape) -> np.ndarray:
-    rng = np.random.default_rng([int(seed), 77, int(side), int(node)])
-    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0)
 
 
 def _range_basis(Z: np.ndarray, r: int) -> np.ndarray:
@@ -71,11 +67,12 @@ def middle_level(apply, apply_adj, N: int, L: int, r: int, p: int = OVERSAMPLE, 
     nb = N // m
     k = min(r + p, nb)
     rk = min(r, nb)
+    Cb, Rb = sketch_blocks(N, L, r, p, seed)
     C = np.zeros((N, m * k), dtype=np.complex128)
     R = np.zeros((N, m * k), dtype=np.complex128)
     for j in range(m):
-        C[j * nb:(j + 1) * nb, j * k:(j + 1) * k] = _gaussian(seed, 0, j, (nb, k))
-        R[j * nb:(j + 1) * nb, j * k:(j + 1) * k] = _gaussian(seed, 1, j, (nb, k))
+        C[j * nb:(j + 1) * nb, j * k:(j + 1) * k] = Cb[j]
+        R[j * nb:(j + 1) * nb, j * k:(j + 1) * k] = Rb[j]
     Y = np.asarray(apply(C))          # slab j, rows of node i: K_ij C_jj
     W = np.asarray(apply_adj(R))      # slab i, rows of node j: K_ij^* R_ii
     U = [[None] * m for _ in range(m)]

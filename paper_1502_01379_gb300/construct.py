@@ -1,0 +1,144 @@
+"""Butterfly factorization from fast applies, on the device (Sec. 3.1, first
+case; Sec. 2.1; Sec. 3.2).
+
+The matrix is known only through products with K and K^* -- typically this
+library's own apply of a factorization composed with other fast operators:
+Example 3 (Sec. 4) factorizes K F K from two applies of K and an FFT.  All m^2
+middle-level blocks K^h_{i,j} are served by 2 m (r + p) products with block-
+diagonal Gaussian matrices (C: K_ij C_jj in rows of node i of slab j; R:
+K_ij^* R_ii in rows of node j of slab i), which go through the black box as
+batches of vectors (the tensor-core path of `bf_apply` for m (r + p) >= 32).
+The per-block randomized SVDs (Sec. 2.1) and the recursive factorization of
+U^h and V^h (Sec. 3.2, all 2^L stacks of a level at once) are batched FP64
+decompositions on the device (torch.linalg).
+
+Readings:
+* Sec. 2.1's step 2 takes the first r columns of Q of a pivoted QR of each
+  sketch; here the range basis is the sketch's r leading left singular
+  vectors (batched pivoted QR is not available on the device).  Both are
+  orthonormal bases of a dominant r-dimensional range of the same sketch.
+* Step 3's middle matrix is formed from the products already taken:
+  M = pinv(R_ii^* Q_col) (W_ij^* Q_row), since W_ij^* = R_ii^* K_ij.
+* p = 5 (Sec. 2.1, Sec. 4), capped at the block size; the Gaussian blocks are
+  ``bfinputs.sketch_blocks`` (seeded, drawn on the host).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from bfinputs.factors import ButterflyFactors, tree_sizes
+from bfinputs.workloads import sketch_blocks
+
+from . import capi
+
+OVERSAMPLE = 5
+SIGMA_TOL = 1e-14
+
+
+def _pad_last(x, size: int):
+    import torch
+    if x.shape[-1] == size:
+        return x
+    pad = torch.zeros(x.shape[:-1] + (size - x.shape[-1],), dtype=x.dtype, device=x.device)
+    return torch.cat([x, pad], dim=-1)
+
+
+def _recursive(X, L: int, r: int):
+    """Sec. 3.2 on all nodes at once.  X[i, j] = U^h_{i,j} (rows of row node i,
+    one entry per column node j); returns the leaf blocks U^L_{a,0} and the
+    transfer blocks G^l in canonical order (block (2i + c) 2^{L-l-1} + j')."""
+    import torch
+    trans = []
+    h = L // 2
+    for _ in range(h, L):
+        ni, nj, rows, _ = X.shape
+        Z = torch.cat([X[:, 0::2], X[:, 1::2]], dim=-1)               # [U_{i,2j'}  U_{i,2j'+1}]
+        half = rows // 2
+        Z = Z.reshape(ni, nj // 2, 2, half, 2 * r)                   # top (c = 0) and bottom (c = 1) halves
+        U0, s, Vh = torch.linalg.svd(Z, full_matrices=False)
+        kk = min(r, s.shape[-1])
+        Unew = _pad_last(U0[..., :kk] * s[..., None, :kk], r)        # U^{l+1} = U_0 Sigma_0
+        Gb = Vh[..., :kk, :]                                          # G^l = V_0^*
+        if kk < r:
+            Gb = torch.cat([Gb, torch.zeros(Gb.shape[:-2] + (r - kk, 2 * r), dtype=Gb.dtype, device=Gb.device)],
+                           dim=-2)
+        trans.append(Gb.permute(0, 2, 1, 3, 4).reshape(ni * 2 * (nj // 2), r, 2 * r))
+        X = Unew.permute(0, 2, 1, 3, 4).reshape(ni * 2, nj // 2, half, r)
+    return X[:, 0], trans
+
+
+def construct_from_applies(apply, apply_adj, N: int, L: int, r: int, p: int = OVERSAMPLE, seed: int = 0,
+                           device="cuda") -> ButterflyFactors:
+    """Factors of the N x N matrix given by ``apply(X)`` = rows of X times K^T,
+    i.e. K applied to each row of X ((nvec, N) complex tensors on ``device``,
+    the layout of `bf_apply`), and ``apply_adj`` likewise for K^*.  Returns the
+    factors in canonical layout (complex128 host arrays), ready for
+    `bf_plan_create`."""
+    import torch
+    if N % (1 << L) or L % 2:
+        raise ValueError("N must be a multiple of 2^L with L even")
+    n0 = N >> L
+    sz = tree_sizes(L, n0, r)
+    h, m = sz["h"], sz["m"]
+    nb = N // m
+    k = min(r + p, nb)
+    rk = min(r, nb)
+    cdt = torch.complex128
+    Cb, Rb = (torch.from_numpy(a).to(device) for a in sketch_blocks(N, L, r, p, seed))   # (m, nb, k)
+    idx = torch.arange(m, device=device)
+    C = torch.zeros((m, k, m, nb), dtype=cdt, device=device)
+    C[idx, :, idx, :] = Cb.transpose(1, 2)                   # vector (j, c) is C_jj[:, c] on node j
+    R = torch.zeros((m, k, m, nb), dtype=cdt, device=device)
+    R[idx, :, idx, :] = Rb.transpose(1, 2)
+    Y = apply(C.reshape(m * k, N)).to(cdt).reshape(m, k, m, nb)        # Y[j, c, i, :] = (K_ij C_jj)[:, c]
+    W = apply_adj(R.reshape(m * k, N)).to(cdt).reshape(m, k, m, nb)    # W[i, c, j, :] = (K_ij^* R_ii)[:, c]
+    Yb = Y.permute(2, 0, 3, 1)                                  # [i, j] = K_ij C_jj      (nb x k)
+    Wb = W.permute(0, 2, 3, 1)                                  # [i, j] = K_ij^* R_ii    (nb x k)
+    Qc = torch.linalg.svd(Yb, full_matrices=False)[0][..., :rk]
+    Qr = torch.linalg.svd(Wb, full_matrices=False)[0][..., :rk]
+    A = Rb.conj().transpose(-1, -2)[:, None] @ Qc               # R_ii^* Q_col
+    M = torch.linalg.pinv(A) @ (Wb.conj().transpose(-1, -2) @ Qr)
+    UM, s, VMh = torch.linalg.svd(M)
+    U0 = Qc @ UM
+    V0 = Qr @ VMh.conj().transpose(-1, -2)
+    keep = s > SIGMA_TOL * s[..., :1]                           # Eq. lowrankSVD, pseudo-inverse for tiny sigma
+    sk = torch.where(keep, s, torch.zeros_like(s))
+    U = _pad_last(U0 * sk[..., None, :].to(cdt), r)             # U = U_0 Sigma_0
+    V = _pad_last(V0 * sk[..., None, :].to(cdt), r)             # V = V_0 Sigma_0
+    S = _pad_last(torch.where(keep, 1.0 / torch.where(keep, s, torch.ones_like(s)), torch.zeros_like(s)), r)
+    UL, G = _recursive(U, L, r)                                 # U side: X[i, j] = U_ij
+    VL, H = _recursive(V.transpose(0, 1), L, r)                 # V side: X[j, i] = V_ij
+    host = lambda t: t.detach().cpu().numpy()
+    meta = {"source": "construct_from_applies", "p": p, "seed": seed, "vectors_per_direction": m * k}
+    return ButterflyFactors(L, n0, r, host(VL), [host(t) for t in H], host(S).astype(np.float64),
+                            [host(t) for t in G], host(UL), meta).validate()
+
+
+def plan_black_box(plan):
+    """(apply, apply_adj) of a `bf_plan` for `construct_from_applies`: rows of a
+    (nvec, N) device tensor through `bf_apply` / `bf_apply_adjoint` in complex64."""
+    import torch
+
+    def run(fn, X):
+        x = X.to(torch.complex64).contiguous()
+        y = torch.empty_like(x)
+        fn(plan, x, y)
+        return y
+    return (lambda X: run(capi.bf_apply, X)), (lambda X: run(capi.bf_apply_adjoint, X))
+
+
+def fourier_rows(X):
+    """F applied to each row: F_{kj} = exp(-2 pi i (k - N/2) j / N) / N (the
+    Fourier-integral quadrature of Example 3), F x = fft((-1)^j x) / N."""
+    import torch
+    N = X.shape[-1]
+    sign = 1.0 - 2.0 * (torch.arange(N, device=X.device) % 2)
+    return torch.fft.fft(X * sign, dim=-1) / N
+
+
+def fourier_adjoint_rows(Y):
+    """F^* y = (-1)^j ifft(y)_j for each row."""
+    import torch
+    N = Y.shape[-1]
+    sign = 1.0 - 2.0 * (torch.arange(N, device=Y.device) % 2)
+    return torch.fft.ifft(Y, dim=-1) * sign

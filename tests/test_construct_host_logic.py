@@ -1,0 +1,63 @@
+"""The construction from applies (`construct_from_applies`): its batched
+linear algebra checked on the host with an exact dense black box, against
+the FP64 oracle of the same algorithm (`oracle.construct_mv`, which takes the
+same random blocks) and the dense matrix.  The GPU run, with this library's
+apply as the black box, is in test_gpu_construct.py."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from bfinputs import complex_normal
+from oracle import apply as A
+from oracle import construct_mv as CM
+from oracle import kernel as KK
+from oracle.kernel import rel_err
+from paper_1502_01379_gb300 import construct as DC
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _box(K):
+    Kt = torch.from_numpy(K)
+    return (lambda X: X @ Kt.T), (lambda X: X @ Kt.conj())
+
+
+def test_full_rank_is_exact():
+    N, L, r = 64, 4, 16
+    K = KK.dense_matrix(N, "fio")
+    F = DC.construct_from_applies(*_box(K), N, L, r, device="cpu")
+    g = complex_normal((N, 2), seed=1)
+    assert rel_err(A.bf_apply(F, g), K @ g) < 1e-12
+    assert rel_err(A.bf_adjoint(F, g), K.conj().T @ g) < 1e-12
+
+
+def test_accuracy_tracks_the_oracle():
+    """N = 1024, one point per leaf, r = 4, 6, 8: within a factor 3 of the
+    oracle's construction from the same products (the SVD range basis is, if
+    anything, the better one)."""
+    N, L = 1024, 10
+    K = KK.dense_matrix(N, "fio")
+    g = complex_normal((N,), seed=3)
+    for r in (4, 6, 8):
+        Fd = DC.construct_from_applies(*_box(K), N, L, r, device="cpu")
+        Fo = CM.construct(lambda X: K @ X, lambda X: K.conj().T @ X, N, L, r)
+        ed, eo = rel_err(A.bf_apply(Fd, g), K @ g), rel_err(A.bf_apply(Fo, g), K @ g)
+        assert ed <= 3 * eo and eo <= 3 * ed, (r, ed, eo)
+        assert Fd.meta["vectors_per_direction"] == Fo.meta["vectors_per_direction"]
+
+
+def test_example3_composition():
+    N, L = 256, 8
+    K = KK.dense_matrix(N, "fio")
+    Kt = K @ CM.fourier_matrix(N) @ K
+    Km = torch.from_numpy(K)
+    app = lambda X: DC.fourier_rows(X @ Km.T) @ Km.T
+    adj = lambda X: DC.fourier_adjoint_rows(X @ Km.conj()) @ Km.conj()
+    g = complex_normal((N,), seed=7)
+    x = torch.from_numpy(g)[None]
+    assert rel_err(app(x)[0].numpy(), Kt @ g) < 1e-13
+    assert rel_err(adj(x)[0].numpy(), Kt.conj().T @ g) < 1e-13
+    e = {r: rel_err(A.bf_apply(DC.construct_from_applies(app, adj, N, L, r, device="cpu"), g), Kt @ g)
+         for r in (4, 8, 12)}
+    assert e[8] < e[4] / 5 and e[12] < e[8] / 50 and e[12] < 1e-4
