@@ -20,12 +20,18 @@
 // consecutive or 4^{L-l-1} apart; the first splitting pass reads the merging
 // half's output transposed (M^h).
 //
-// Kernel: one thread block per (group, tile of NT right-hand sides); the
-// input stack (Kin x NT) is staged in shared memory; thread o accumulates
-// output o of the stack for the NT vectors in FP32 while it streams column o
-// of F (stored k-major, F^T, so a warp's loads of one k are contiguous).  One
-// vector at a time this is a stream over the factors (HBM-bound); with NT = 32
-// every factor entry feeds 32 complex multiply-adds.
+// Kernels.  Thread o of a group accumulates output o of the stack in FP32
+// while it streams column o of F (stored k-major, F^T, so a warp's loads of
+// one k are contiguous), the input stack staged in shared memory:
+//  * one vector (quad_gemv_kernel): one group per thread block, a stream over
+//    the blocks (HBM-bound);
+//  * 2..31 vectors and the two levels that touch the caller's vectors in
+//    larger calls (quad_pass_kernel<NT>): tiles of NT vectors, several groups
+//    per block for small stacks, planar-tile outputs staged through shared
+//    memory;
+//  * 32 or more vectors: every other level on the tensor-core core
+//    (bf_tc.cuh, LD_QUAD / ST_QUAD, launched through bf_internal.h), with
+//    planar 128-vector tiles between all levels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
