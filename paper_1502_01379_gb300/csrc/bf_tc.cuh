@@ -32,7 +32,18 @@
 // of adding up pass after pass.  X_lo lives next to X in tensor memory; the
 // prep warp rounds each streamed F in shared memory and builds F_lo there.
 // A plan may instead ask for plain TF32 products (split = 1: one MMA per
-// product, no low parts), a faster and less accurate rung of the ladder.
+// product, no low parts), or for BF16 operands (kind::f16, K = 16 per MMA,
+// the template flag BF): plain, hi/lo (3 products) or a three-way split
+// hi + mid + lo (6 products); the BF16 blocks are split once per plan into
+// their parts (bf16_split_kernel) and streamed as they are, the activations
+// are split by the epilogue warps as they enter tensor memory.
+//
+// 2D levels (LD_QUAD / ST_QUAD): the same item pipeline on one quadtree level
+// of a 2D factorization -- a group's four input blocks gathered as runs of
+// positions, its stack split into output parts and K-chunks of at most 64;
+// the K-chunks of a work item are consecutive sub-items of one CTA that
+// accumulate in tensor memory, and the epilogue reads D and E after the last.
+// Items whose tile fits half the staging area get two staging buffers.
 //
 // Tensor memory (512 columns): Re X | Im X | Re X_lo | Im X_lo (64 each) |
 // D (128) | E (128).  BF16 operands pack two values per column, so each X
