@@ -1405,16 +1405,20 @@ bf_status bf_batch_check(bf_batch B, cudaStream_t stream) {
 
 int bf_batch_items(bf_batch B) { return B ? B->nitems : 0; }
 
-// The tensor-core blocks of both directions split into `parts` BF16 parts
-// (0: none kept).  All new buffers are allocated before anything is
-// released, so on BF_ERR_NOMEM the plan is unchanged.  Synchronous: the
-// splits run on the legacy default stream and are waited for.
-static bf_status set_bf16_blocks(bf_plan_s &P, int parts) {
+// The tensor-core blocks of both directions split into the BF16 parts of the
+// rung (split, bf16) (no parts kept for a TF32 rung), and the rung recorded.
+// All new buffers are allocated before anything is released, so on
+// BF_ERR_NOMEM the plan is unchanged; once they are installed the plan's rung
+// is set to match them before any split runs, so a failure after that point
+// can leave wrong values but never a rung that reads more parts than a buffer
+// holds.  Synchronous: the splits run on the legacy default stream and are
+// waited for.
+static bf_status set_bf16_blocks(bf_plan_s &P, int split, int bf16) {
+    const int parts = bf16 ? (split == 6 ? 3 : split == 3 ? 2 : 1) : 0;
     std::vector<WidePass *> todo;
     for (WideDirection *D : {&P.tfwd, &P.tadj})
         for (auto &wp : D->pass)
             if (wp.d16_parts != parts) todo.push_back(&wp);
-    if (todo.empty()) return BF_OK;
     auto part_bytes = [&](const WidePass &wp) {
         return (size_t)P.m * wp.ngroups * 2 * wp.Nout * wp.Kin * sizeof(uint16_t);
     };
@@ -1426,15 +1430,21 @@ static bf_status set_bf16_blocks(bf_plan_s &P, int parts) {
                 for (uint16_t *q : fresh) cudaFree(q);
                 return BF_ERR_NOMEM;
             }
-    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaErrorUnknown);   // no launch reads the old parts
+    if (!todo.empty() && cudaDeviceSynchronize() != cudaSuccess)   // no launch reads the old parts
+        return cuda_fail(cudaErrorUnknown);
     for (size_t i = 0; i < todo.size(); ++i) {
         WidePass &wp = *todo[i];
         cudaFree(wp.d16);
         P.device_bytes -= part_bytes(wp) * wp.d16_parts;
         wp.d16 = fresh[i];
         wp.d16_parts = parts;
-        if (parts == 0) continue;
         P.device_bytes += part_bytes(wp) * parts;
+    }
+    P.tc_split = split;
+    P.tc_bf16 = bf16;
+    if (parts == 0 || todo.empty()) return BF_OK;
+    for (WidePass *w : todo) {
+        WidePass &wp = *w;
         const long long nblocks = (long long)P.m * wp.ngroups;
         const long long chunks = nblocks * 2 * wp.Nout * wp.Kin / 8;
         const int grid = (int)std::min<long long>((chunks + 255) / 256, 8LL * P.num_sms);
@@ -1457,11 +1467,7 @@ bf_status bf_plan_set_precision(bf_plan plan, int precision) {
     case BF_PREC_BF16X6: split = 6; bf16 = 1; break;
     default: return BF_ERR_INVALID;
     }
-    const bf_status st = set_bf16_blocks(*plan, bf16 ? (split == 6 ? 3 : split == 3 ? 2 : 1) : 0);
-    if (st != BF_OK) return st;
-    plan->tc_split = split;
-    plan->tc_bf16 = bf16;
-    return BF_OK;
+    return set_bf16_blocks(*plan, split, bf16);
 }
 
 bf_status bf_batch_destroy(bf_batch B) {

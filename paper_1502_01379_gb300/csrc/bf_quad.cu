@@ -652,22 +652,25 @@ bf_status bf_quad_set_precision(bf_quad Q, int precision) {
                 for (uint16_t *q : fresh) cudaFree(q);
                 return BF_ERR_NOMEM;
             }
-    if (cudaDeviceSynchronize() != cudaSuccess) return qfail(cudaErrorUnknown);
+    if (!todo.empty() && cudaDeviceSynchronize() != cudaSuccess) return qfail(cudaErrorUnknown);
     for (size_t i = 0; i < todo.size(); ++i) {
         bfq::HostPass &hp = *todo[i];
         cudaFree(hp.d16);
         Q->device_bytes -= part_bytes(hp) * hp.d16_parts;
         hp.d16 = fresh[i];
         hp.d16_parts = parts;
-        if (parts == 0) continue;
         Q->device_bytes += part_bytes(hp) * parts;
-        if (bfint::bf16_split(hp.dtc, hp.d16, (long long)hp.p.nA * hp.p.nB * hp.parts * hp.chunks, 2 * hp.Nc, hp.Kc,
-                              parts, Q->num_sms) != cudaSuccess)
-            return qfail(cudaErrorUnknown);
     }
-    if (cudaDeviceSynchronize() != cudaSuccess) return qfail(cudaErrorUnknown);
+    // the rung matches the installed buffers before any split runs: a failure
+    // below can leave wrong values, never a rung reading more parts than exist
     Q->tc_split = split;
     Q->tc_bf16 = bf16;
+    if (parts == 0 || todo.empty()) return BF_OK;
+    for (bfq::HostPass *hp : todo)
+        if (bfint::bf16_split(hp->dtc, hp->d16, (long long)hp->p.nA * hp->p.nB * hp->parts * hp->chunks, 2 * hp->Nc,
+                              hp->Kc, parts, Q->num_sms) != cudaSuccess)
+            return qfail(cudaErrorUnknown);
+    if (cudaDeviceSynchronize() != cudaSuccess) return qfail(cudaErrorUnknown);
     return BF_OK;
 }
 
