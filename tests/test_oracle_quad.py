@@ -140,3 +140,19 @@ def test_exactness_pin_catches_planted_mistakes():
     order = np.arange(nb).reshape(nb // 4, 4)[:, ::-1].reshape(-1)
     assert broken(lambda G: G.G.__setitem__(0, F.G[0][order])) > 1e-3
     assert broken(lambda G: G.UL.__setitem__(slice(None), F.UL[::-1])) > 1e-3
+
+
+def test_dft2_factorization_against_the_fft():
+    """The 2D DFT (Phi = x.xi) factorized by the 2D construction and applied,
+    against numpy's ifft2: within 10 eps of the construction, and improving
+    with r (the 2D DFT's blocks have product ranks, so it needs more rank than
+    the 1D DFT)."""
+    n, L = 16, 4
+    g = complex_normal((n * n,), seed=2)
+    ref = Q.dft2_closed_form(g, n)
+    errs = {}
+    for r in (4, 8):
+        F = Q.construct(n, L, r, "dft2", seed=1)
+        errs[r] = rel_err(Q.bf_apply(F, g), ref)
+        assert errs[r] <= 10 * F.meta["eps"]
+    assert errs[8] < errs[4] / 5
