@@ -21,6 +21,19 @@ Readings:
   M = pinv(R_ii^* Q_col) (W_ij^* Q_row), since W_ij^* = R_ii^* K_ij.
 * p = 5 (Sec. 2.1, Sec. 4), capped at the block size; the Gaussian blocks are
   ``bfinputs.sketch_blocks`` (seeded, drawn on the host).
+
+Two ways to take the decompositions (``method``):
+* "svd" (default): batched SVDs of the tall sketches and stacks.
+* "gram": the same bases from the small Hermitian Gram matrices -- the
+  leading eigenvectors V_r of Z^* Z (k x k or 2r x 2r, batched eigh) give
+  U_0 Sigma_0 = Z V_r and V_0^* = V_r^* directly, and the sketch's range basis
+  is Z V_r Lambda_r^{-1/2} re-orthonormalized once; only batched matrix
+  products touch the tall matrices.  Forming Z^* Z squares the conditioning,
+  so directions below 1e-7 of the largest singular value are dropped (the
+  noise floor of FP32 products anyway): this form's accuracy bottoms out near
+  1e-7 where "svd" reaches roundoff.  Batched SVDs of many tall complex
+  matrices run one matrix at a time in the device libraries, small batched
+  eigensolves do not, so this is the form meant for large N.
 """
 from __future__ import annotations
 
@@ -33,6 +46,7 @@ from . import capi
 
 OVERSAMPLE = 5
 SIGMA_TOL = 1e-14
+GRAM_TOL = 1e-14
 
 
 def _pad_last(x, size: int):
@@ -43,7 +57,33 @@ def _pad_last(x, size: int):
     return torch.cat([x, pad], dim=-1)
 
 
-def _recursive(X, L: int, r: int):
+def _top_eig(Z, r: int):
+    """Leading r eigenpairs (descending) of Z^* Z for a batch of tall Z."""
+    import torch
+    lam, V = torch.linalg.eigh(Z.conj().transpose(-1, -2) @ Z)
+    lam = torch.flip(lam, dims=[-1])[..., :r].clamp_min(0.0)
+    V = torch.flip(V, dims=[-1])[..., :r]
+    return lam, V
+
+
+def _range_basis(Z, r: int, method: str):
+    """Orthonormal basis of the dominant r-dimensional range of each Z (Sec. 2.1, step 2)."""
+    import torch
+    if method == "svd":
+        return torch.linalg.svd(Z, full_matrices=False)[0][..., :r]
+    lam, V = _top_eig(Z, r)
+    # directions below GRAM_TOL of the largest eigenvalue (singular-value ratio
+    # 1e-7, the noise floor of FP32 products) are dropped: zero columns
+    keep = lam > GRAM_TOL * lam[..., :1]
+    scale = torch.where(keep, torch.rsqrt(torch.where(keep, lam, torch.ones_like(lam))), torch.zeros_like(lam))
+    Q1 = (Z @ V) * scale[..., None, :].to(Z.dtype)
+    lam2, V2 = torch.linalg.eigh(Q1.conj().transpose(-1, -2) @ Q1)          # one re-orthonormalization:
+    keep2 = lam2 > 0.5                                                        # ~1 for kept, ~0 for dropped
+    scale2 = torch.where(keep2, torch.rsqrt(torch.where(keep2, lam2, torch.ones_like(lam2))), torch.zeros_like(lam2))
+    return Q1 @ (V2 * scale2[..., None, :].to(Z.dtype))
+
+
+def _recursive(X, L: int, r: int, method: str = "svd"):
     """Sec. 3.2 on all nodes at once.  X[i, j] = U^h_{i,j} (rows of row node i,
     one entry per column node j); returns the leaf blocks U^L_{a,0} and the
     transfer blocks G^l in canonical order (block (2i + c) 2^{L-l-1} + j')."""
@@ -55,10 +95,15 @@ def _recursive(X, L: int, r: int):
         Z = torch.cat([X[:, 0::2], X[:, 1::2]], dim=-1)               # [U_{i,2j'}  U_{i,2j'+1}]
         half = rows // 2
         Z = Z.reshape(ni, nj // 2, 2, half, 2 * r)                   # top (c = 0) and bottom (c = 1) halves
-        U0, s, Vh = torch.linalg.svd(Z, full_matrices=False)
-        kk = min(r, s.shape[-1])
-        Unew = _pad_last(U0[..., :kk] * s[..., None, :kk], r)        # U^{l+1} = U_0 Sigma_0
-        Gb = Vh[..., :kk, :]                                          # G^l = V_0^*
+        kk = min(r, half, 2 * r)
+        if method == "svd":
+            U0, s, Vh = torch.linalg.svd(Z, full_matrices=False)
+            Unew = _pad_last(U0[..., :kk] * s[..., None, :kk], r)    # U^{l+1} = U_0 Sigma_0
+            Gb = Vh[..., :kk, :]                                      # G^l = V_0^*
+        else:
+            _, V = _top_eig(Z, kk)
+            Unew = _pad_last(Z @ V, r)                                # Z V_r = U_0 Sigma_0
+            Gb = V.conj().transpose(-1, -2)
         if kk < r:
             Gb = torch.cat([Gb, torch.zeros(Gb.shape[:-2] + (r - kk, 2 * r), dtype=Gb.dtype, device=Gb.device)],
                            dim=-2)
@@ -68,13 +113,15 @@ def _recursive(X, L: int, r: int):
 
 
 def construct_from_applies(apply, apply_adj, N: int, L: int, r: int, p: int = OVERSAMPLE, seed: int = 0,
-                           device="cuda") -> ButterflyFactors:
+                           device="cuda", method: str = "svd") -> ButterflyFactors:
     """Factors of the N x N matrix given by ``apply(X)`` = rows of X times K^T,
     i.e. K applied to each row of X ((nvec, N) complex tensors on ``device``,
     the layout of `bf_apply`), and ``apply_adj`` likewise for K^*.  Returns the
     factors in canonical layout (complex128 host arrays), ready for
-    `bf_plan_create`."""
+    `bf_plan_create`.  ``method``: "svd" or "gram" (see the module docstring)."""
     import torch
+    if method not in ("svd", "gram"):
+        raise ValueError("method must be 'svd' or 'gram'")
     if N % (1 << L) or L % 2:
         raise ValueError("N must be a multiple of 2^L with L even")
     n0 = N >> L
@@ -94,8 +141,8 @@ def construct_from_applies(apply, apply_adj, N: int, L: int, r: int, p: int = OV
     W = apply_adj(R.reshape(m * k, N)).to(cdt).reshape(m, k, m, nb)    # W[i, c, j, :] = (K_ij^* R_ii)[:, c]
     Yb = Y.permute(2, 0, 3, 1)                                  # [i, j] = K_ij C_jj      (nb x k)
     Wb = W.permute(0, 2, 3, 1)                                  # [i, j] = K_ij^* R_ii    (nb x k)
-    Qc = torch.linalg.svd(Yb, full_matrices=False)[0][..., :rk]
-    Qr = torch.linalg.svd(Wb, full_matrices=False)[0][..., :rk]
+    Qc = _range_basis(Yb, rk, method)
+    Qr = _range_basis(Wb, rk, method)
     A = Rb.conj().transpose(-1, -2)[:, None] @ Qc               # R_ii^* Q_col
     M = torch.linalg.pinv(A) @ (Wb.conj().transpose(-1, -2) @ Qr)
     UM, s, VMh = torch.linalg.svd(M)
@@ -106,10 +153,11 @@ def construct_from_applies(apply, apply_adj, N: int, L: int, r: int, p: int = OV
     U = _pad_last(U0 * sk[..., None, :].to(cdt), r)             # U = U_0 Sigma_0
     V = _pad_last(V0 * sk[..., None, :].to(cdt), r)             # V = V_0 Sigma_0
     S = _pad_last(torch.where(keep, 1.0 / torch.where(keep, s, torch.ones_like(s)), torch.zeros_like(s)), r)
-    UL, G = _recursive(U, L, r)                                 # U side: X[i, j] = U_ij
-    VL, H = _recursive(V.transpose(0, 1), L, r)                 # V side: X[j, i] = V_ij
+    UL, G = _recursive(U, L, r, method)                         # U side: X[i, j] = U_ij
+    VL, H = _recursive(V.transpose(0, 1), L, r, method)         # V side: X[j, i] = V_ij
     host = lambda t: t.detach().cpu().numpy()
-    meta = {"source": "construct_from_applies", "p": p, "seed": seed, "vectors_per_direction": m * k}
+    meta = {"source": "construct_from_applies", "p": p, "seed": seed, "vectors_per_direction": m * k,
+            "method": method}
     return ButterflyFactors(L, n0, r, host(VL), [host(t) for t in H], host(S).astype(np.float64),
                             [host(t) for t in G], host(UL), meta).validate()
 

@@ -61,3 +61,25 @@ def test_example3_composition():
     e = {r: rel_err(A.bf_apply(DC.construct_from_applies(app, adj, N, L, r, device="cpu"), g), Kt @ g)
          for r in (4, 8, 12)}
     assert e[8] < e[4] / 5 and e[12] < e[8] / 50 and e[12] < 1e-4
+
+
+def test_gram_form_matches_svd_form_down_to_its_floor():
+    """method="gram" (small batched Hermitian eigensolves instead of tall
+    SVDs): the same accuracy as "svd" wherever the factorization's error is
+    above ~1e-7 (r = 4, 6, 8 at N = 1024), and a graceful floor near 1e-7
+    where "svd" reaches roundoff (r = 12 here; full rank at N = 64)."""
+    N, L = 1024, 10
+    K = KK.dense_matrix(N, "fio")
+    g = complex_normal((N,), seed=3)
+    for r in (4, 6, 8):
+        es = rel_err(A.bf_apply(DC.construct_from_applies(*_box(K), N, L, r, device="cpu"), g), K @ g)
+        eg = rel_err(A.bf_apply(DC.construct_from_applies(*_box(K), N, L, r, device="cpu", method="gram"), g), K @ g)
+        assert abs(eg - es) <= 0.05 * es, (r, es, eg)
+    e12 = rel_err(A.bf_apply(DC.construct_from_applies(*_box(K), N, L, 12, device="cpu", method="gram"), g), K @ g)
+    assert e12 < 1e-6
+    K64 = KK.dense_matrix(64, "fio")
+    g64 = complex_normal((64,), seed=1)
+    F = DC.construct_from_applies(*_box(K64), 64, 4, 16, device="cpu", method="gram")
+    assert rel_err(A.bf_apply(F, g64), K64 @ g64) < 1e-6
+    with pytest.raises(ValueError):
+        DC.construct_from_applies(*_box(K64), 64, 4, 16, device="cpu", method="qr")
