@@ -32,6 +32,8 @@ if ROOT not in sys.path:
 
 METRIC = "butterfly apply vectors/s at N=2^20 r=16 (apply + adjoint, complex64)"
 FALLBACK_HBM_GBS = 6800.0
+MIN_CLOCK_S = 0.6          # the headline's K-step region is repeated until it covers this long
+MAX_REGIONS = 200
 
 
 def parse_args(argv=None):
@@ -230,12 +232,23 @@ def run_ours(args, rank, world, local):
             dev_id = "GPU-" + dev_id
     except Exception:
         pass
+    # The timed region is exactly K steps.  It is repeated back to back until
+    # the regions cover at least MIN_CLOCK_S seconds, so the clock sampler
+    # (50 ms period) sees the GPU under this load many times; the median
+    # region gives the value, every region's kernel times the roofline.
     sampler = ClockSampler(dev_id) if rank == 0 else None
     t_clk0 = time.time()
-    ms, kt = timed(g, u, v, nrhs, args.steps, args.warmup, profile=True)
+    regions, kt = [], {"down": (0, 0.0), "up": (0, 0.0)}
+    while True:
+        ms_r, kt_r = timed(g, u, v, nrhs, args.steps, args.warmup if not regions else 0, profile=True)
+        regions.append(ms_r)          # max over ranks: every rank takes the same decision below
+        kt = {k: (kt[k][0] + kt_r[k][0], kt[k][1] + kt_r[k][1]) for k in kt}
+        if sum(regions) >= MIN_CLOCK_S * 1e3 or len(regions) >= MAX_REGIONS:
+            break
     t_clk1 = time.time()
     if sampler:
         sampler.stop()
+    ms = statistics.median(regions)
     value, ms_tot = aggregate([ms], [2 * nrhs * args.steps * world])
     ms_per_step = ms_tot / args.steps
 
@@ -319,6 +332,10 @@ def run_ours(args, rank, world, local):
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "vectors/s", "h2d_bytes_per_step": 2 * N * nrhs * 8,
                 "d2h_bytes_per_step": 2 * N * nrhs * 8},
+        "timed_regions": {"count": len(regions), "ms_each_median": ms, "ms_each_min": min(regions),
+                          "ms_each_max": max(regions),
+                          "note": "each region = exactly K steps bracketed by barrier + synchronize; value from "
+                                  "the median region; regions repeated so the clock samples cover >= 0.6 s"},
         "gpu_launches": 4 * chunks * args.steps,
         "clocks": sampler.summary(t_clk0, t_clk1) if sampler else None,
         "nrhs_sweep": sweep_out,

@@ -44,7 +44,14 @@ typedef enum {
 
 /* Shape of a factorization.  Compiled limits: L even, 0 <= L <= 24;
  * 1 <= r <= 32; 1 <= leaf <= 64; and m * max(leaf, r) <= 8192 (one tree
- * node's vector segment must fit in shared memory). */
+ * node's vector segment must fit in shared memory).
+ * There is no arity field: a 1D factorization (binary trees, this struct
+ * with bf_plan_create) and a 2D one (quadtrees, the same struct with
+ * bf_quad_create) have different factor shapes and different plans, so the
+ * entry point chosen states the arity.  There is no precision field either:
+ * factors are always stored in complex64 (FP32), and the operand precision
+ * of the tensor-core path is a property of a plan that can change between
+ * calls (bf_plan_set_precision), not of the factorization's shape. */
 typedef struct {
     int L;          /* depth of T_X and T_Omega, even (Sec. 1.2)                     */
     int leaf;       /* n0 = N / 2^L, points per leaf node (Sec. 3, "bounded leaf")  */
@@ -99,7 +106,8 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
  *            vector at a time through the fused single-RHS kernels (up to 4
  *            per thread block), 8..31 through the CUDA-core multi-RHS core,
  *            32 or more through the tensor-core core (bf_plan_set_precision).
- * in and out must not overlap (BF_ERR_INVALID).  One plan owns one
+ * in and out must not overlap (BF_ERR_INVALID).  The calling thread's
+ * current device must be the plan's (BF_ERR_INVALID otherwise).  One plan owns one
  * workspace: calls on the same plan must not run concurrently on different
  * streams. */
 bf_status bf_apply(bf_plan plan, const void *in, void *out, int nrhs, long long ld,
@@ -147,10 +155,16 @@ bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms
  *   Limit    2^L * r (one vector's level-h data) must be <= 2^21, else
  *            BF_ERR_UNSUPPORTED; larger batches run in passes of
  *            floor(2^21 / (2^L r)) vectors.
+ *   Device   the calling thread's current device must be the one the plan
+ *            was created on (BF_ERR_INVALID otherwise): the array is per
+ *            device, the plan's factors are on one.
  * Every GPU that loads the library holds the 16 MiB array until the process
  * exits.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  All calls share the one array, which
+ * (cudaGetSymbolAddress, with that device current) and caches it with the
+ * identity of the device's context, so after a cudaDeviceReset (which ends
+ * the context; plans made before it are gone with it) the next call looks it
+ * up again; make the first call on a device, and the first after a reset,
+ * before any stream capture.  All calls share the one array, which
  * keeps the last call's contents (each pass overwrites what it reads, so
  * nothing needs clearing): calls that overlap on the GPU -- on different
  * streams, or from different threads -- race and give wrong results. */

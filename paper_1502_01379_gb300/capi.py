@@ -36,6 +36,16 @@ class BfError(RuntimeError):
         self.status = status
 
 
+class BfArgumentError(BfError, ValueError):
+    """An argument the wrapper rejects before calling the library (status
+    BF_ERR_INVALID, as the C ABI would report it, but raised for checks the
+    ABI cannot make: buffer sizes, dtypes and devices)."""
+
+    def __init__(self, msg: str):
+        RuntimeError.__init__(self, f"{msg}: BF_ERR_INVALID (status {BF_ERR_INVALID})")
+        self.status = BF_ERR_INVALID
+
+
 class bf_desc(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("leaf", ctypes.c_int), ("r", ctypes.c_int), ("nrhs_max", ctypes.c_int)]
 
@@ -158,8 +168,9 @@ def _addr(x) -> int:
 class Plan:
     """Owns a bf_plan handle and the host arrays kept alive during creation."""
 
-    def __init__(self, handle: int, N: int, L: int, n0: int, r: int, nrhs_max: int):
+    def __init__(self, handle: int, N: int, L: int, n0: int, r: int, nrhs_max: int, device: int | None = None):
         self.handle, self.N, self.L, self.n0, self.r, self.nrhs_max = handle, N, L, n0, r, nrhs_max
+        self.device = device          # CUDA device index the plan was created on
 
     def __del__(self):
         try:
@@ -200,15 +211,59 @@ def bf_plan_create(factors, nrhs_max: int = 1, stream=None) -> Plan:
                                  ctypes.c_void_p(_stream_handle(stream))), "bf_plan_create")
     del keep
     return Plan(h.value, int(factors.n0) << int(factors.L), int(factors.L), int(factors.n0),
-                int(factors.r), int(nrhs_max))
+                int(factors.r), int(nrhs_max), _current_device())
 
 
-def _vec_args(plan: Plan, x, y, nrhs, ld):
+def _current_device():
+    """torch's current CUDA device index, or None without CUDA."""
+    try:
+        import torch
+        return int(torch.cuda.current_device()) if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
+def _check_vec(what: str, v, plan, nrhs: int, ld: int, device_only: bool) -> None:
+    """The kernels read and write (nrhs - 1) * ld + N complex64 entries through
+    a bare pointer, and the C ABI cannot see the buffer's size: check dtype,
+    device and element count here, before the call.  Raw integer addresses
+    are the caller's responsibility."""
+    if isinstance(v, int):
+        return
+    need = (nrhs - 1) * ld + plan.N if nrhs > 0 else 0
+    if isinstance(v, np.ndarray):
+        if v.dtype != np.complex64:
+            raise BfArgumentError(f"{what}: complex64 array required, got {v.dtype}")
+        if device_only:
+            raise BfArgumentError(f"{what}: a device tensor is required (host arrays are not accepted here)")
+        if v.size < need:
+            raise BfArgumentError(f"{what}: holds {v.size} entries, the call needs (nrhs-1)*ld+N = {need}")
+        return
+    import torch
+    if not isinstance(v, torch.Tensor):
+        raise BfArgumentError(f"{what}: expected a torch tensor, numpy array or integer address, got {type(v).__name__}")
+    if v.dtype != torch.complex64:
+        raise BfArgumentError(f"{what}: complex64 tensor required, got {v.dtype}")
+    if v.is_cuda:
+        if plan.device is not None and v.device.index != plan.device:
+            raise BfArgumentError(f"{what}: tensor on cuda:{v.device.index}, plan on cuda:{plan.device}")
+    elif device_only:
+        raise BfArgumentError(f"{what}: a device tensor is required (host tensors are not accepted here)")
+    if v.numel() < need:
+        raise BfArgumentError(f"{what}: holds {v.numel()} entries, the call needs (nrhs-1)*ld+N = {need}")
+
+
+def _vec_args(plan, x, y, nrhs, ld, device_only: bool = False):
     if nrhs is None:
-        nrhs = 1 if x.ndim == 1 else int(x.shape[0])
+        nrhs = 1 if isinstance(x, int) or x.ndim == 1 else int(x.shape[0])
     if ld is None:
         ld = plan.N
-    return _addr(x), _addr(y), int(nrhs), int(ld)
+    nrhs, ld = int(nrhs), int(ld)
+    if nrhs < 0 or ld < plan.N:
+        raise BfArgumentError(f"nrhs must be >= 0 and ld >= N = {plan.N} (got nrhs={nrhs}, ld={ld})")
+    _check_vec("input", x, plan, nrhs, ld, device_only)
+    _check_vec("output", y, plan, nrhs, ld, device_only)
+    return _addr(x), _addr(y), nrhs, ld
 
 
 def bf_apply(plan: Plan, x, y, nrhs: int | None = None, ld: int | None = None, stream=None) -> None:
@@ -228,8 +283,9 @@ def bf_apply_adjoint(plan: Plan, x, y, nrhs: int | None = None, ld: int | None =
 class QuadPlan:
     """Owns a bf_quad handle (2D factorization on quadtrees)."""
 
-    def __init__(self, handle: int, N: int, L: int, n0: int, r: int, nrhs_max: int):
+    def __init__(self, handle: int, N: int, L: int, n0: int, r: int, nrhs_max: int, device: int | None = None):
         self.handle, self.N, self.L, self.n0, self.r, self.nrhs_max = handle, N, L, n0, r, nrhs_max
+        self.device = device          # CUDA device index the plan was created on
 
     def __del__(self):
         try:
@@ -253,13 +309,13 @@ def bf_quad_create(factors, nrhs_max: int = 1, stream=None) -> QuadPlan:
                                  ctypes.c_void_p(_stream_handle(stream))), "bf_quad_create")
     del keep
     return QuadPlan(h.value, int(factors.n0) << (2 * int(factors.L)), int(factors.L), int(factors.n0),
-                    int(factors.r), int(nrhs_max))
+                    int(factors.r), int(nrhs_max), _current_device())
 
 
 def bf_quad_apply(plan: QuadPlan, x, y, nrhs: int | None = None, ld: int | None = None, adjoint: bool = False,
                   stream=None) -> None:
     """y = K_bf x (or K_bf^* x) for a 2D plan; device tensors (asynchronous)."""
-    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
+    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld, device_only=True)
     _check(load().bf_quad_apply(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi), n, l,
                                 1 if adjoint else 0, ctypes.c_void_p(_stream_handle(stream))), "bf_quad_apply")
 
@@ -330,7 +386,7 @@ def bf_apply_static_scratch(plan: Plan, x, y, nrhs: int | None = None, ld: int |
     """y = K_bf x (or K_bf^* x) without any device allocation: the
     intermediate vector lives in the library's fixed 16 MiB device array.
     Device tensors only; calls that overlap on the GPU race."""
-    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld)
+    xi, yi, n, l = _vec_args(plan, x, y, nrhs, ld, device_only=True)
     _check(load().bf_apply_static_scratch(ctypes.c_void_p(plan.handle), ctypes.c_void_p(xi), ctypes.c_void_p(yi),
                                           n, l, 1 if adjoint else 0, ctypes.c_void_p(_stream_handle(stream))),
            "bf_apply_static_scratch")

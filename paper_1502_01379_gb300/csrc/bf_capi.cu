@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -72,6 +73,7 @@ struct WideDirection {
 
 struct bf_plan_s {
     int L, n0, r, h, m, W, nrhs_max;
+    int device = -1;                              // CUDA device the plan's memory lives on
     long long N, R;
     int stages, slot_len, consumers;
     Direction fwd, adj;
@@ -813,6 +815,37 @@ bool is_host_pointer(const void *p) {
     return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
+// True when the calling thread's current device is the one the plan was
+// created on (its factors, workspaces and error word live there).
+bool on_plan_device(const bf_plan_s &P) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return dev == P.device;
+}
+
+// The two host-pointer staging buffers (N x nrhs_max each), allocated on
+// first use.  Both are installed together or not at all, so a failed second
+// allocation never leaves a plan with one buffer and a null partner.
+bf_status ensure_staging(bf_plan_s &P) {
+    if (P.d_stage_in && P.d_stage_out) return BF_OK;
+    const size_t bytes = (size_t)P.N * P.nrhs_max * sizeof(float2);
+    float2 *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMalloc(&a, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        cudaFree(b);
+        return cuda_fail(e);
+    }
+    P.d_stage_in = a;
+    P.d_stage_out = b;
+    P.device_bytes += 2 * bytes;
+    return BF_OK;
+}
+
 bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cudaStream_t s, bool adjoint) {
     if (!P || !in || !out || nrhs < 0 || ld < P->N) return BF_ERR_INVALID;
     if (nrhs == 0) return BF_OK;
@@ -820,13 +853,12 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
     const char *ob = static_cast<const char *>(out);
     const long long span = ((long long)(nrhs - 1) * ld + P->N) * 8;
     if (ib < ob + span && ob < ib + span) return BF_ERR_INVALID;
+    if (!on_plan_device(*P)) return BF_ERR_INVALID;
     const Direction &D = adjoint ? P->adj : P->fwd;
     const bool host_in = is_host_pointer(in), host_out = is_host_pointer(out);
-    if ((host_in || host_out) && !P->d_stage_in) {
-        const size_t bytes = (size_t)P->N * P->nrhs_max * sizeof(float2);
-        BF_CUDA(cudaMalloc(&P->d_stage_in, bytes));
-        BF_CUDA(cudaMalloc(&P->d_stage_out, bytes));
-        P->device_bytes += 2 * bytes;
+    if (host_in || host_out) {
+        const bf_status st = ensure_staging(*P);
+        if (st != BF_OK) return st;
     }
     for (int c0 = 0; c0 < nrhs; c0 += P->nrhs_max) {
         const int nc = std::min(P->nrhs_max, nrhs - c0);
@@ -848,12 +880,8 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
             // dimension; others go through the (aligned) staging buffers.
             auto aligned = [](const void *q, long long l) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0 && (l & 1) == 0; };
             if (!aligned(src, ld_in) || !aligned(kdst, ld_out)) {
-                if (!P->d_stage_in) {
-                    const size_t bytes = (size_t)P->N * P->nrhs_max * sizeof(float2);
-                    BF_CUDA(cudaMalloc(&P->d_stage_in, bytes));
-                    BF_CUDA(cudaMalloc(&P->d_stage_out, bytes));
-                    P->device_bytes += 2 * bytes;
-                }
+                const bf_status st = ensure_staging(*P);
+                if (st != BF_OK) return st;
                 if (!aligned(src, ld_in)) {
                     BF_CUDA(cudaMemcpy2DAsync(P->d_stage_in, P->N * 8, src, ld_in * 8, P->N * 8, nc,
                                               cudaMemcpyDeviceToDevice, s));
@@ -898,22 +926,59 @@ static __device__ __align__(256) float2 bf_static_scratch[kStaticScratchEntries]
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-void *g_scratch_address[kMaxDevices] = {};
+struct ScratchAddress {
+    unsigned long long ctx_id = 0;   // context the address belongs to (0: none looked up yet)
+    void *p = nullptr;
+};
+ScratchAddress g_scratch_address[kMaxDevices];
+
+// Identity of the calling thread's current context (cuCtxGetCurrent +
+// cuCtxGetId through the runtime's driver entry points); 0 if unavailable.
+// A device reset destroys the primary context, and the one the runtime makes
+// next has a new identity, so an address looked up before the reset is
+// never reused after it.
+unsigned long long current_context_id() {
+    using GetCurrentFn = CUresult (*)(CUcontext *);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+    static const std::pair<GetCurrentFn, GetIdFn> fns = [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            a = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            b = nullptr;
+        cudaGetLastError();
+        return std::make_pair(reinterpret_cast<GetCurrentFn>(a), reinterpret_cast<GetIdFn>(b));
+    }();
+    if (!fns.first || !fns.second) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (fns.first(&ctx) != CUDA_SUCCESS || !ctx || fns.second(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of bf_static_scratch on the current device.  The host-side
-// name of the array is only a stand-in; the address is looked up once per
-// device (with that device current) and cached.
+// name of the array is only a stand-in; the address is looked up with the
+// device current (cudaGetSymbolAddress, return code checked) the first time
+// a device's context is seen, and cached per device together with that
+// context's identity.  If the identity cannot be read, it is looked up on
+// every call.
 bf_status static_scratch_address(float2 **out) {
     int dev = 0;
     BF_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return BF_ERR_UNSUPPORTED;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_address[dev]) {
+    ScratchAddress &c = g_scratch_address[dev];
+    if (ctx == 0 || c.ctx_id != ctx || !c.p) {
         void *p = nullptr;
         BF_CUDA(cudaGetSymbolAddress(&p, bf_static_scratch));
-        g_scratch_address[dev] = p;
+        c.p = p;
+        c.ctx_id = ctx;
     }
-    *out = static_cast<float2 *>(g_scratch_address[dev]);
+    *out = static_cast<float2 *>(c.p);
     return BF_OK;
 }
 
@@ -990,6 +1055,10 @@ bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, c
     P->nrhs_max = desc->nrhs_max;
     P->N = (long long)n0 << L;
     P->R = (1LL << L) * r;
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        delete P;
+        return cuda_fail(cudaErrorInvalidDevice);
+    }
     if ((long long)P->m * P->W > 8192) {
         delete P;
         return BF_ERR_UNSUPPORTED;
@@ -1176,6 +1245,7 @@ bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int n
     const long long span = ((long long)(nrhs - 1) * ld + P->N) * 8;
     if (ib < ob + span && ob < ib + span) return BF_ERR_INVALID;
     if (is_host_pointer(in) || is_host_pointer(out)) return BF_ERR_INVALID;   // staging would allocate
+    if (!on_plan_device(*P)) return BF_ERR_INVALID;   // the scratch address is per device
     float2 *ws = nullptr;
     bf_status st = static_scratch_address(&ws);
     if (st != BF_OK) return st;

@@ -222,6 +222,7 @@ struct bf_quad_s {
     int tc_split = 3, tc_bf16 = 0;
     int kc_max = 64;          // tensor-core K-chunk limit (BF_QUAD_KC: 32 or 64)
     int inject_stall = 0;     // failure-detection test hook (BF_INJECT_STALL=1 at creation)
+    int device = -1;          // CUDA device the plan's memory lives on
     unsigned *d_err = nullptr;
 };
 
@@ -518,6 +519,7 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
     Q->Rmax = pow4(L) * Q->ranks[Q->h];
     int dev = 0;
     cudaGetDevice(&dev);
+    Q->device = dev;
     cudaDeviceGetAttribute(&Q->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (const char *e = std::getenv("BF_TC_MIN")) Q->tc_min = std::max(8, std::atoi(e));   // planar tiles need NT >= 8
     Q->tc = Q->nrhs_max >= Q->tc_min;
@@ -565,6 +567,11 @@ bf_status bf_quad_apply(bf_quad Q, const void *in, void *out, int nrhs, long lon
     const long long span = ((long long)(nrhs - 1) * ld + Q->N) * 8;
     if (a < b + span && b < a + span) return BF_ERR_INVALID;
     if (!is_device_ptr(in) || !is_device_ptr(out)) return BF_ERR_INVALID;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != Q->device) {   // the plan's memory is on Q->device
+        cudaGetLastError();
+        return BF_ERR_INVALID;
+    }
     const auto &D = adjoint ? Q->adj : Q->fwd;
     const int np = (int)D.size();
     for (int k0 = 0; k0 < nrhs; k0 += Q->nrhs_max) {

@@ -93,3 +93,60 @@ def test_null_arguments(lib):
     assert lib.bf_plan_device_bytes(None) == 0
     assert lib.bf_plan_check(None, None) == capi.BF_ERR_INVALID
     assert lib.bf_plan_set_profiling(None, 1) == capi.BF_ERR_INVALID
+
+
+# ---------------------------------------------------- wrapper-side buffer checks
+# The kernels read (nrhs-1)*ld + N complex64 entries through a bare pointer;
+# the Python wrapper is the only place that can see the buffers' sizes, dtypes
+# and devices, so it must reject bad ones before any call reaches the library.
+def _fake_plan(N=64):
+    return capi.Plan(0, N, 4, N >> 4, 2, 1, device=0)
+
+
+@pytest.mark.parametrize("case", ["x_c128", "y_short", "nrhs_too_big", "y_float", "ld_small", "nrhs_negative"])
+def test_wrapper_rejects_bad_vectors_before_the_call(lib, case):
+    torch = pytest.importorskip("torch")
+    P = _fake_plan()
+    x = np.zeros((2, P.N), np.complex64)
+    y = np.zeros((2, P.N), np.complex64)
+    kw = {}
+    if case == "x_c128":
+        x = x.astype(np.complex128)
+    elif case == "y_short":
+        y = y[:1]
+    elif case == "nrhs_too_big":
+        kw = dict(nrhs=3)
+    elif case == "y_float":
+        x, y = torch.from_numpy(x), torch.zeros(2 * P.N, dtype=torch.float32)
+    elif case == "ld_small":
+        kw = dict(nrhs=1, ld=P.N - 1)
+    elif case == "nrhs_negative":
+        kw = dict(nrhs=-1)
+    for fn in (capi.bf_apply, capi.bf_apply_adjoint):
+        with pytest.raises(capi.BfArgumentError) as e:
+            fn(P, x, y, **kw)
+        assert e.value.status == capi.BF_ERR_INVALID
+        assert isinstance(e.value, ValueError)
+
+
+def test_wrapper_rejects_host_buffers_where_device_ones_are_required(lib):
+    torch = pytest.importorskip("torch")
+    P = _fake_plan()
+    x = torch.zeros((1, P.N), dtype=torch.complex64)
+    for call in (lambda: capi.bf_apply_static_scratch(P, x, torch.empty_like(x)),
+                 lambda: capi.bf_quad_apply(P, x, torch.empty_like(x)),
+                 lambda: capi.bf_quad_apply(P, x.numpy(), np.empty_like(x.numpy()))):
+        with pytest.raises(capi.BfArgumentError):
+            call()
+
+
+def test_wrapper_passes_well_formed_buffers_to_the_library(lib):
+    """Correct buffers get past the wrapper; the library itself then rejects
+    the null plan handle (status BF_ERR_INVALID, not a wrapper error)."""
+    P = _fake_plan()
+    x = np.zeros((3, P.N + 5), np.complex64)
+    y = np.zeros((3, P.N + 5), np.complex64)
+    with pytest.raises(capi.BfError) as e:
+        capi.bf_apply(P, x, y, nrhs=3, ld=P.N + 5, stream=0)
+    assert not isinstance(e.value, capi.BfArgumentError)
+    assert e.value.status == capi.BF_ERR_INVALID
