@@ -381,6 +381,41 @@ bf_status bf_quad_destroy(bf_quad plan);
 bf_status bf_quad_set_precision(bf_quad plan, int precision);
 bf_status bf_quad_check(bf_quad plan, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Sketch products of a 1D kernel matrix, for the construction from products
+ * (Sec. 3.1, first case; the randomized SVD of Sec. 2.1 needs K_ij C_jj and
+ * K_ij^* R_ii for Gaussian blocks supported on one middle-level node each).
+ * The matrix is K(x_j, xi_k) = exp(2 pi i (x_j xi_k + c_j |xi_k|)) with
+ * x_j = j/N, xi_k = k - N/2 (Sec. 4, Eq. 1D-FIO-kernal: Example 1 has
+ * c_j = (2 + sin 2 pi x_j)/8; c = 0 is the Fourier matrix of Sec. 1.1 up to
+ * the column shift).  Entries are generated on the fly (exact fixed-point
+ * phase reduction modulo 1, FP32 sin/cos and sums): O(N^2 k) work, nothing
+ * of K is stored.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int log2N;          /* N = 2^log2N, 1 <= log2N <= 30                          */
+    int nb;             /* rows of one sketch block: a power of two <= N          */
+    int k;              /* columns of a sketch block, 1 <= k <= 32                */
+    int node0, nodes;   /* blocks used: node0 .. node0 + nodes - 1 (nodes <= 65535)*/
+    long long lo, hi;   /* output index range, 0 <= lo < hi <= N                  */
+    int adjoint;        /* 0: products with K; otherwise with K^*                 */
+} bf_sketch_desc;
+
+/* With b < nodes, c < k, o in [lo, hi), n = node0 + b:
+ *   adjoint = 0:  out[(b k + c)(hi - lo) + o - lo] = sum_t K(o, n nb + t) blocks[(b nb + t) k + c]
+ *   adjoint != 0: out[(b k + c)(hi - lo) + o - lo] = sum_t conj(K(n nb + t, o)) blocks[(b nb + t) k + c]
+ * over t < nb: block b is a sketch block on column node n (forward) or row
+ * node n (adjoint), and only the output rows [lo, hi) are formed.
+ *   c_fixed  DEVICE array of N unsigned 64-bit integers c_j 2^64 (c_j in [0, 1)
+ *            as a fixed-point fraction), or NULL for c = 0.
+ *   blocks   DEVICE complex64, nodes x nb x k (row-major), caller-owned.
+ *   out      DEVICE complex64, nodes x k x (hi - lo), caller-owned, must not
+ *            overlap blocks.
+ * Asynchronous on `stream`; allocates nothing.  BF_ERR_INVALID for bad
+ * sizes, ranges or host pointers; BF_ERR_UNSUPPORTED for k > 32. */
+bf_status bf_sketch_products(const bf_sketch_desc *desc, const unsigned long long *c_fixed,
+                             const void *blocks, void *out, cudaStream_t stream);
+
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);
 

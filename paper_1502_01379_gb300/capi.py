@@ -25,7 +25,7 @@ EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", 
            "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
            "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision", "bf_quad_create",
            "bf_quad_apply", "bf_quad_device_bytes", "bf_quad_passes", "bf_quad_destroy", "bf_quad_tc_passes",
-           "bf_quad_set_precision", "bf_quad_check")
+           "bf_quad_set_precision", "bf_quad_check", "bf_sketch_products")
 BF_PREC_FP32, BF_PREC_TF32, BF_PREC_BF16X3, BF_PREC_BF16, BF_PREC_BF16X6 = 0, 1, 2, 3, 4
 BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
@@ -65,6 +65,12 @@ bf_dgrads = bf_dfactors   # same shape: device pointers (written by the backward
 
 class bf_batch_config(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("slot_kb", ctypes.c_int), ("stages", ctypes.c_int)]
+
+
+class bf_sketch_desc(ctypes.Structure):
+    _fields_ = [("log2N", ctypes.c_int), ("nb", ctypes.c_int), ("k", ctypes.c_int), ("node0", ctypes.c_int),
+                ("nodes", ctypes.c_int), ("lo", ctypes.c_longlong), ("hi", ctypes.c_longlong),
+                ("adjoint", ctypes.c_int)]
 
 
 class bf_diff_desc(ctypes.Structure):
@@ -117,6 +123,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "bf_quad_tc_passes": (i, [vp]),
         "bf_quad_set_precision": (i, [vp, i]),
         "bf_quad_check": (i, [vp, vp]),
+        "bf_sketch_products": (i, [ctypes.POINTER(bf_sketch_desc), vp, vp, vp, vp]),
         "bf_diff_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_diff_desc)]),
         "bf_diff_destroy": (i, [vp]),
         "bf_diff_stride": (i, [vp]),
@@ -525,3 +532,27 @@ def bf_batch_items(batch: Batch) -> int:
 
 def bf_batch_destroy(batch: Batch) -> None:
     batch.destroy()
+
+
+# ------------------------------------------------------------ sketch products
+def bf_sketch_products(log2N: int, nb: int, blocks, out, lo: int, hi: int, node0: int = 0,
+                       adjoint: bool = False, c_fixed=None, stream=None) -> None:
+    """Products of K(x_j, xi_k) = exp(2 pi i (x_j xi_k + c_j |xi_k|)) (or K^*)
+    with sketch blocks, rows [lo, hi) of the result (include/bfly.h).
+    ``blocks``: (nodes, nb, k) complex64 device tensor; ``out``: (nodes, k,
+    hi - lo) complex64 device tensor; ``c_fixed``: (N,) int64 device tensor
+    holding c_j 2^64 as unsigned bits, or None for c = 0."""
+    import torch
+    for name, t, shape in (("blocks", blocks, None), ("out", out, None)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+            raise BfArgumentError(f"{name}: contiguous complex64 device tensor required")
+    nodes, nbb, k = blocks.shape
+    if nbb != nb or tuple(out.shape) != (nodes, k, hi - lo):
+        raise BfArgumentError(f"shapes: blocks {tuple(blocks.shape)}, out {tuple(out.shape)}, nb {nb}, rows {hi - lo}")
+    if c_fixed is not None and (not isinstance(c_fixed, torch.Tensor) or c_fixed.dtype != torch.int64 or
+                                not c_fixed.is_cuda or c_fixed.numel() != (1 << log2N)):
+        raise BfArgumentError("c_fixed: (N,) int64 device tensor required")
+    d = bf_sketch_desc(int(log2N), int(nb), int(k), int(node0), int(nodes), int(lo), int(hi), 1 if adjoint else 0)
+    _check(load().bf_sketch_products(ctypes.byref(d), ctypes.c_void_p(0 if c_fixed is None else c_fixed.data_ptr()),
+                                     ctypes.c_void_p(blocks.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(_stream_handle(stream))), "bf_sketch_products")

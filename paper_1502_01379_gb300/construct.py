@@ -190,3 +190,226 @@ def fourier_adjoint_rows(Y):
     N = Y.shape[-1]
     sign = 1.0 - 2.0 * (torch.arange(N, device=Y.device) % 2)
     return torch.fft.ifft(Y, dim=-1) * sign
+
+
+# --------------------------------------------------------------------------
+# Analytic 1D kernels at large N: sketches by entry evaluation, chunked passes
+# --------------------------------------------------------------------------
+KERNEL_KINDS = ("fio", "dft")
+EPS_FLOOR = 1e-7          # FP32 sketch products: the construction's noise floor
+
+
+def c_fixed_point(kind: str, N: int):
+    """c_j 2^64 as int64 bit patterns for K = exp(2 pi i (x xi + c(x)|xi|)):
+    Example 1's c(x) = (2 + sin 2 pi x)/8 at x_j = j/N (Eq. 1D-FIO-kernal), or
+    None for the Fourier matrix (c = 0).  Exact: an FP64 c in [2^-12, 1) times
+    2^64 is an integer."""
+    if kind == "dft":
+        return None
+    if kind != "fio":
+        raise ValueError(f"unknown kernel kind {kind!r}")
+    c = (2.0 + np.sin(2.0 * np.pi * (np.arange(N, dtype=np.float64) / N))) / 8.0
+    mant, ex = np.frexp(c)                                    # c = mant 2^ex, mant in [0.5, 1)
+    M = np.ldexp(mant, 53).astype(np.uint64)                  # 53-bit integer mantissa, exact
+    out = M << (ex + 11).astype(np.uint64)                    # c 2^64 = M 2^(ex + 11), ex in [-2, -1]
+    return out.view(np.int64)
+
+
+def _gram_basis(Z, rk: int):
+    """For each tall Z (batched): the k x rk coefficients T with Z T an
+    orthonormal basis of Z's dominant rk-dimensional range (Sec. 2.1, step 2,
+    from the Gram matrix: leading eigenvectors scaled by 1/sqrt(eigenvalue),
+    one re-orthonormalization), the Gram matrix Z^* Z itself, and the
+    normalized tail sqrt(lambda_{rk+1} / lambda_1) (0 if Z has <= rk columns)."""
+    import torch
+    Gz = Z.conj().transpose(-1, -2) @ Z
+    lam, V = torch.linalg.eigh(Gz)
+    lam = torch.flip(lam, dims=[-1]).clamp_min(0.0)
+    V = torch.flip(V, dims=[-1])
+    top = lam[..., :1].clamp_min(1e-300)
+    tail = torch.sqrt(lam[..., rk] / top[..., 0]) if lam.shape[-1] > rk else torch.zeros_like(top[..., 0])
+    lam, V = lam[..., :rk], V[..., :rk]
+    keep = lam > GRAM_TOL * top
+    T1 = V * torch.where(keep, torch.rsqrt(torch.where(keep, lam, torch.ones_like(lam))),
+                         torch.zeros_like(lam))[..., None, :].to(Z.dtype)
+    Q1 = Z @ T1
+    lam2, V2 = torch.linalg.eigh(Q1.conj().transpose(-1, -2) @ Q1)
+    keep2 = lam2 > 0.5
+    T = T1 @ (V2 * torch.where(keep2, torch.rsqrt(torch.where(keep2, lam2, torch.ones_like(lam2))),
+                               torch.zeros_like(lam2))[..., None, :].to(Z.dtype))
+    return T, Gz, tail
+
+
+def _recursive_gram(X, r: int):
+    """Sec. 3.2 (Gram form) on a chunk of middle-level nodes: X[i, j] (rows of
+    node i, one entry per node j of the other tree).  Returns the leaf blocks,
+    the transfer blocks of every level (chunk-local canonical order) and the
+    largest normalized tail sigma_{r+1} / sigma_1 over the level stacks."""
+    import torch
+    trans = []
+    eps = 0.0
+    while X.shape[1] > 1:
+        ni, nj, rows, _ = X.shape
+        Z = torch.cat([X[:, 0::2], X[:, 1::2]], dim=-1)
+        half = rows // 2
+        Z = Z.reshape(ni, nj // 2, 2, half, 2 * r)
+        kk = min(r, half, 2 * r)
+        lam, V = torch.linalg.eigh(Z.conj().transpose(-1, -2) @ Z)
+        lam = torch.flip(lam, dims=[-1]).clamp_min(0.0)
+        V = torch.flip(V, dims=[-1])[..., :kk]
+        if 2 * r > kk:
+            tail = torch.sqrt(lam[..., kk] / lam[..., 0].clamp_min(1e-300))
+            eps = max(eps, float(tail.max()))
+        Unew = _pad_last(Z @ V, r)                                    # Z V_r = U_0 Sigma_0
+        Gb = V.conj().transpose(-1, -2)                               # V_0^*
+        if kk < r:
+            Gb = torch.cat([Gb, torch.zeros(Gb.shape[:-2] + (r - kk, 2 * r), dtype=Gb.dtype, device=Gb.device)],
+                           dim=-2)
+        trans.append(Gb.permute(0, 2, 1, 3, 4).reshape(ni * 2 * (nj // 2), r, 2 * r))
+        X = Unew.permute(0, 2, 1, 3, 4).reshape(ni * 2, nj // 2, half, r)
+    return X[:, 0], trans, eps
+
+
+def construct_kernel_1d(kind: str, N: int, L: int, r: int, p: int = OVERSAMPLE, seed: int = 0, chunk: int = 16,
+                        device="cuda", out_dtype=np.complex64, stream=None) -> ButterflyFactors:
+    """Butterfly factorization of K(x_j, xi_k) = exp(2 pi i (x_j xi_k + c(x_j)|xi_k|))
+    (``kind`` "fio": Example 1; "dft": c = 0, the Fourier matrix) from sketch
+    products (Sec. 3.1, first case; Sec. 2.1; Sec. 3.2), at sizes where no
+    dense K and no whole-level array fits: the products are formed by
+    `bf_sketch_products` (entries generated on the GPU) and the work runs in
+    two passes over chunks of ``chunk`` middle-level nodes.
+
+    U pass, row nodes I: K_ij C_jj for i in I (rows of I, every column node j)
+    and K_ij^* R_ii (every column); per block the Gram-form range bases
+    Qc = Y Tc, Qr = W Tr, the middle matrix M = pinv(R_ii^* Qc)(W^* Qr) and its
+    SVD U_M Sigma V_M^* (Eq. lowrankSVD); U_ij = Y (Tc U_M Sigma), the recursive
+    factorization of the U side under I.  Only the k x r coefficients
+    Z_ij = Tr V_M Sigma and S_ij = Sigma^{-1} are kept.  V pass, column nodes
+    J: K_ij^* R_ii for j in J again (the same products, bit for bit: each
+    output is one fixed-order sum), V_ij = W Z_ij -- the middle level's own
+    SVD, not a second one -- and the recursive factorization of the V side.
+    Memory is O(chunk N k) on the device; factors go to the host per chunk.
+
+    Returns factors (``out_dtype`` host arrays) whose ``meta`` holds the phase
+    timings and the construction's epsilon = max(eps_mid, eps_rec, EPS_FLOOR):
+    eps_mid the largest normalized (r+1)-th singular value of a middle-block
+    sketch, eps_rec the largest normalized tail of a recursive stack."""
+    import time
+
+    import torch
+    if kind not in KERNEL_KINDS:
+        raise ValueError(f"kind must be one of {KERNEL_KINDS}")
+    if N & (N - 1) or N % (1 << L) or L % 2:
+        raise ValueError("N must be a power of two, a multiple of 2^L, L even")
+    log2N = N.bit_length() - 1
+    n0 = N >> L
+    h = L // 2
+    m = 1 << h
+    nb = N // m
+    k = min(r + p, nb)
+    rk = min(r, nb)
+    chunk = max(1, min(chunk, m))
+    cdt = torch.complex128
+    t = {"sketch_s": 0.0, "middle_s": 0.0, "recursive_s": 0.0, "host_s": 0.0}
+    on_gpu = torch.device(device).type == "cuda"
+    sync = torch.cuda.synchronize if on_gpu else (lambda: None)
+    t0 = time.perf_counter()
+    Cb, Rb = sketch_blocks(N, L, r, p, seed)                     # (m, nb, k) complex128, host
+    C32 = torch.from_numpy(Cb.astype(np.complex64)).to(device)
+    R32 = torch.from_numpy(Rb.astype(np.complex64)).to(device)
+    # the exact inputs of the sketch products, for R_ii^* K_ij = W^*: the
+    # complex64-rounded blocks the products used
+    R64 = R32.to(cdt)
+    del Cb, Rb
+    cf = c_fixed_point(kind, N)
+    cfix = None if cf is None else torch.from_numpy(cf).to(device)
+    t["inputs_s"] = time.perf_counter() - t0
+    VL = np.empty((1 << L, n0, r), out_dtype)
+    UL = np.empty((1 << L, n0, r), out_dtype)
+    H = [np.empty((1 << L, r, 2 * r), out_dtype) for _ in range(h)]
+    G = [np.empty((1 << L, r, 2 * r), out_dtype) for _ in range(h)]
+    S = np.empty((m, m, r), np.float64)
+    Zc = torch.empty((m, m, k, r), dtype=cdt, device=device)    # V_ij = W_ij Zc[i, j]
+    eps_mid = eps_rec = 0.0
+    cast = lambda x: x.detach().cpu().numpy().astype(out_dtype, copy=False)
+
+    def sketch(blocks, node0, lo, hi, adjoint):
+        out = torch.empty((blocks.shape[0], k, hi - lo), dtype=torch.complex64, device=device)
+        capi.bf_sketch_products(log2N, nb, blocks, out, lo, hi, node0=node0, adjoint=adjoint, c_fixed=cfix,
+                                stream=stream)
+        return out
+
+    # ---- U pass
+    for i0 in range(0, m, chunk):
+        ci = min(chunk, m - i0)
+        a = time.perf_counter()
+        Yf = sketch(C32, 0, i0 * nb, (i0 + ci) * nb, False)                 # (m_j, k, ci nb)
+        Wf = sketch(R32[i0:i0 + ci].contiguous(), i0, 0, N, True)           # (ci, k, N)
+        sync()
+        b = time.perf_counter()
+        Y = Yf.reshape(m, k, ci, nb).permute(2, 0, 3, 1).to(cdt)           # [i, j] = K_ij C_jj  (nb x k)
+        del Yf
+        W = Wf.reshape(ci, k, m, nb).permute(0, 2, 3, 1).to(cdt)           # [i, j] = K_ij^* R_ii (nb x k)
+        del Wf
+        Tc, _, tail_c = _gram_basis(Y, rk)
+        Tr, Gw, tail_r = _gram_basis(W, rk)
+        eps_mid = max(eps_mid, float(tail_c.max()), float(tail_r.max()))
+        RY = R64[i0:i0 + ci, None].conj().transpose(-1, -2) @ Y            # R_ii^* K_ij C_jj   (k x k)
+        A = RY @ Tc                                                          # R_ii^* Qc
+        M = torch.linalg.pinv(A) @ (Gw @ Tr)                                 # pinv(R^* Qc) (W^* Qr)
+        UM, s, VMh = torch.linalg.svd(M)
+        keep = s > SIGMA_TOL * s[..., :1]
+        sk = torch.where(keep, s, torch.zeros_like(s)).to(cdt)
+        Xc = _pad_last((Tc @ UM) * sk[..., None, :], r)                      # U_ij = Y Xc
+        Zc[i0:i0 + ci] = _pad_last((Tr @ VMh.conj().transpose(-1, -2)) * sk[..., None, :], r)
+        Sblk = _pad_last(torch.where(keep, 1.0 / torch.where(keep, s, torch.ones_like(s)), torch.zeros_like(s)), r)
+        U = Y @ Xc                                                           # (ci, m, nb, r)
+        del Y, W, RY, A, M, Tc, Tr, Gw
+        sync()
+        c = time.perf_counter()
+        ULc, Gc, e = _recursive_gram(U, r)
+        eps_rec = max(eps_rec, e)
+        del U
+        sync()
+        d = time.perf_counter()
+        S[i0:i0 + ci] = Sblk.cpu().numpy()
+        UL[i0 * m:(i0 + ci) * m] = cast(ULc)
+        for lv, blk in enumerate(Gc):
+            G[lv][i0 * m:(i0 + ci) * m] = cast(blk)
+        del ULc, Gc
+        t["sketch_s"] += b - a
+        t["middle_s"] += c - b
+        t["recursive_s"] += d - c
+        t["host_s"] += time.perf_counter() - d
+    # ---- V pass
+    for j0 in range(0, m, chunk):
+        cj = min(chunk, m - j0)
+        a = time.perf_counter()
+        Wv = sketch(R32, 0, j0 * nb, (j0 + cj) * nb, True)                  # (m_i, k, cj nb)
+        sync()
+        b = time.perf_counter()
+        W = Wv.reshape(m, k, cj, nb).permute(2, 0, 3, 1).to(cdt)           # [j, i] = K_ij^* R_ii
+        del Wv
+        V = W @ Zc[:, j0:j0 + cj].transpose(0, 1)                            # [j, i] = V_ij (nb x r)
+        del W
+        sync()
+        c = time.perf_counter()
+        VLc, Hc, e = _recursive_gram(V, r)
+        eps_rec = max(eps_rec, e)
+        del V
+        sync()
+        d = time.perf_counter()
+        VL[j0 * m:(j0 + cj) * m] = cast(VLc)
+        for lv, blk in enumerate(Hc):
+            H[lv][j0 * m:(j0 + cj) * m] = cast(blk)
+        del VLc, Hc
+        t["sketch_s"] += b - a
+        t["middle_s"] += c - b
+        t["recursive_s"] += d - c
+        t["host_s"] += time.perf_counter() - d
+    t["total_s"] = time.perf_counter() - t0
+    eps = max(eps_mid, eps_rec, EPS_FLOOR)
+    meta = {"source": "construct_kernel_1d", "kind": kind, "p": p, "seed": seed, "chunk": chunk,
+            "eps": eps, "eps_mid": eps_mid, "eps_rec": eps_rec, "eps_floor": EPS_FLOOR, "timings": t,
+            "sketch_multiply_adds": 3 * N * N * k}
+    return ButterflyFactors(L, n0, r, VL, H, S, G, UL, meta).validate()
