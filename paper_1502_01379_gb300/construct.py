@@ -215,6 +215,18 @@ def c_fixed_point(kind: str, N: int):
     return out.view(np.int64)
 
 
+def _eigh(A):
+    """Batched Hermitian eigendecomposition (ascending); if the device solver
+    reports a batch element that did not converge, the batch is solved on the
+    host (LAPACK) instead."""
+    import torch
+    try:
+        return torch.linalg.eigh(A)
+    except RuntimeError:
+        lam, V = torch.linalg.eigh(A.cpu())
+        return lam.to(A.device), V.to(A.device)
+
+
 def _gram_basis(Z, rk: int):
     """For each tall Z (batched): the k x rk coefficients T with Z T an
     orthonormal basis of Z's dominant rk-dimensional range (Sec. 2.1, step 2,
@@ -223,7 +235,7 @@ def _gram_basis(Z, rk: int):
     normalized tail sqrt(lambda_{rk+1} / lambda_1) (0 if Z has <= rk columns)."""
     import torch
     Gz = Z.conj().transpose(-1, -2) @ Z
-    lam, V = torch.linalg.eigh(Gz)
+    lam, V = _eigh(Gz)
     lam = torch.flip(lam, dims=[-1]).clamp_min(0.0)
     V = torch.flip(V, dims=[-1])
     top = lam[..., :1].clamp_min(1e-300)
@@ -232,11 +244,16 @@ def _gram_basis(Z, rk: int):
     keep = lam > GRAM_TOL * top
     T1 = V * torch.where(keep, torch.rsqrt(torch.where(keep, lam, torch.ones_like(lam))),
                          torch.zeros_like(lam))[..., None, :].to(Z.dtype)
+    # re-orthonormalization (the second step of Cholesky QR): Q1^* Q1 = R^* R is
+    # close to the identity on the kept columns; dropped columns are zero in T1
+    # and get a unit diagonal so that they stay zero in T1 R^{-1}
     Q1 = Z @ T1
-    lam2, V2 = torch.linalg.eigh(Q1.conj().transpose(-1, -2) @ Q1)
-    keep2 = lam2 > 0.5
-    T = T1 @ (V2 * torch.where(keep2, torch.rsqrt(torch.where(keep2, lam2, torch.ones_like(lam2))),
-                               torch.zeros_like(lam2))[..., None, :].to(Z.dtype))
+    G2 = Q1.conj().transpose(-1, -2) @ Q1
+    G2 = G2 + torch.diag_embed((~keep).to(G2.dtype))
+    Rc, info = torch.linalg.cholesky_ex(G2, upper=True)
+    if bool((info != 0).any()):
+        raise RuntimeError("re-orthonormalization: Gram matrix of the range basis is not positive definite")
+    T = torch.linalg.solve_triangular(Rc, T1, upper=True, left=False)       # T1 R^{-1}
     return T, Gz, tail
 
 
@@ -254,7 +271,7 @@ def _recursive_gram(X, r: int):
         half = rows // 2
         Z = Z.reshape(ni, nj // 2, 2, half, 2 * r)
         kk = min(r, half, 2 * r)
-        lam, V = torch.linalg.eigh(Z.conj().transpose(-1, -2) @ Z)
+        lam, V = _eigh(Z.conj().transpose(-1, -2) @ Z)
         lam = torch.flip(lam, dims=[-1]).clamp_min(0.0)
         V = torch.flip(V, dims=[-1])[..., :kk]
         if 2 * r > kk:

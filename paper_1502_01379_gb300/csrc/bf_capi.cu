@@ -1070,10 +1070,14 @@ bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, c
     P->consumers = cfg.consumers;
     P->inject_stall = env_int("BF_INJECT_STALL", 0) == 1 ? 1 : 0;
     int slot_len = cfg.slot_kb * 128;
-    slot_len = std::max(slot_len, std::max(4 * r * r, n0 * r + 1));
+    const int slot_min = std::max(4 * r * r, n0 * r + 1);
+    slot_len = std::max(slot_len, slot_min);
     P->slot_len = (slot_len + 1) & ~1;
     P->stages = std::max(2, cfg.stages);
     while (P->stages > 2 && plan_smem(*P, 1) > cfg.smem_limit) --P->stages;
+    // Large node segments (m max(n0, r) near 8192) leave less room for the
+    // ring: halve the slots while they still hold a whole unit.
+    while (plan_smem(*P, 1) > cfg.smem_limit && P->slot_len / 2 >= slot_min) P->slot_len = ((P->slot_len / 2) + 1) & ~1;
     if (plan_smem(*P, 1) > cfg.smem_limit) {
         delete P;
         return BF_ERR_UNSUPPORTED;
