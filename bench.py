@@ -51,6 +51,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-operators line")
     ap.add_argument("--no-quad", action="store_true", help="skip the 2D (quadtree) line")
+    ap.add_argument("--no-construct", action="store_true", help="skip the construction line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -351,6 +352,8 @@ def run_ours(args, rank, world, local):
         out["batched"] = batch_line(dev, stream)
     if not args.no_quad:
         out["quad2d"] = quad_line(dev, stream)
+    if not args.no_construct:
+        out["construction"] = construction_line(dev, stream)
     return out
 
 
@@ -489,6 +492,69 @@ def batch_line(dev, stream):
         res["modes"][name] = {"ms_apply_plus_adjoint": ms, "vectors_per_s": vecs / (ms / 1e3)}
     res["graph_vs_each"] = res["modes"]["graph"]["vectors_per_s"] / res["modes"]["each"]["vectors_per_s"]
     b.destroy()
+    return res
+
+
+def construction_line(dev, stream, log2N=18, L=16, r=16):
+    """The construction from sketch products on the GPU (Sec. 3.1 first case,
+    Sec. 2.1, Sec. 3.2): the Fourier matrix and Example 1's FIO at N = 2^18,
+    L = 16 (leaf 4), r = 16, timed per phase; the Fourier factorization's
+    error on every entry of K g against the FFT; and the sketch-product
+    kernel (entries generated on the fly, FP32 multiply-adds) against the
+    FP32 FMA peak.  The N = 2^20 constructions are checked in the GPU tests."""
+    import numpy as np
+    import torch
+
+    import paper_1502_01379_gb300 as bf
+    from paper_1502_01379_gb300 import capi, construct
+    from bfinputs import complex_normal
+    N = 1 << log2N
+    res = {"workload": f"construction from sketch products: DFT and 1D FIO (Example 1), N=2^{log2N}, L={L}, "
+                       f"leaf={N >> L}, r={r}, p=5; FP32 products, FP64 decompositions"}
+    for kind in ("dft", "fio"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F = construct.construct_kernel_1d(kind, N, L, r, seed=1)
+        secs = time.perf_counter() - t0
+        ent = {"seconds": secs, "phases_s": F.meta["timings"], "eps": F.meta["eps"]}
+        if kind == "dft":
+            plan = bf.bf_plan_create(F, nrhs_max=1)
+            g = complex_normal((1, N), seed=4, dtype=np.complex64)
+            x = torch.from_numpy(g).to(dev)
+            y = torch.empty_like(x)
+            bf.bf_apply(plan, x, y, stream=stream)
+            torch.cuda.synchronize()
+            plan.destroy()
+            sign = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+            exact = sign * N * np.fft.ifft(g[0].astype(np.complex128))      # K g, Fourier matrix, by the FFT
+            got = y.cpu().numpy()[0].astype(np.complex128)
+            ent["eps_a_every_entry_vs_fft"] = float(np.linalg.norm(got - exact) / np.linalg.norm(exact))
+        res[kind] = ent
+        del F
+    # the sketch-product kernel alone: one full forward product (every row, every node)
+    m, nb, k = 1 << (L // 2), N >> (L // 2), r + 5
+    blocks = torch.from_numpy(complex_normal((m, nb, k), seed=9, dtype=np.complex64)).to(dev)
+    out = torch.empty((m, k, N), dtype=torch.complex64, device=dev)
+    cfix = torch.from_numpy(construct.c_fixed_point("fio", N)).to(dev)
+    run = lambda: capi.bf_sketch_products(log2N, nb, blocks, out, 0, N, c_fixed=cfix, stream=stream)
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    flops = 8.0 * N * N * k                     # one complex multiply-add (8 flops) per entry and column
+    peak = fp32_fma_peak_tflops(dev)
+    res["sketch_kernel"] = {
+        "kernel": "sketch_kernel", "ms_per_full_product": ms, "entries_per_s": N * N / (ms / 1e3),
+        "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / (ms / 1e3) / 1e12 / peak,
+                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                     "note": "FP32 multiply-add flops of the products only; the entry generation (64-bit phase, "
+                             "sincospif) runs on the same pipes and is not counted"}}
     return res
 
 
