@@ -35,6 +35,7 @@ typedef enum {
     BF_ERR_NOMEM = 3,        /* device or host allocation failed                               */
     BF_ERR_UNSUPPORTED = 4,  /* valid but outside the library's compiled limits (r > 32, ...) */
     BF_ERR_TIMEOUT = 5,      /* a kernel's bounded wait expired; its output is not valid       */
+    BF_ERR_CORRUPT = 6,      /* a factor file failed its checks (magic, sizes, checksums)      */
 } bf_status;
 
 typedef enum {
@@ -415,6 +416,35 @@ typedef struct {
  * sizes, ranges or host pointers; BF_ERR_UNSUPPORTED for k > 32. */
 bf_status bf_sketch_products(const bf_sketch_desc *desc, const unsigned long long *c_fixed,
                              const void *blocks, void *out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Factor files.  Constructing a factorization (Sec. 3) costs far more than
+ * applying it, so a factorization is stored once and planned again later.
+ * A factor file is a 64-byte header -- magic "BFLYFAC", format version (1),
+ * dtype, L, leaf, r, payload size, the CRC-32 of the payload and the CRC-32
+ * of the header's first 44 bytes -- followed by the arrays of bf_factors in
+ * canonical order (VL, H[0..h-1], S, G[0..h-1], UL; S real in the dtype's
+ * precision and zero-padded to a multiple of 8 bytes).  The writer is the
+ * Python binding's `bf_factor_file_save`.  CRC-32 here is ISO-HDLC / IEEE
+ * 802.3 (reflected polynomial 0xEDB88320; "123456789" -> 0xCBF43926).
+ * ------------------------------------------------------------------------- */
+
+/* Reads and verifies a factor file without creating anything: BF_OK and its
+ * shape in *desc (nrhs_max = 0) and dtype in *dtype (either may be NULL);
+ * BF_ERR_CORRUPT for a wrong magic, a header or payload checksum that does
+ * not match, a shape outside the compiled limits, or a file shorter or longer
+ * than its header says; BF_ERR_UNSUPPORTED for another format version;
+ * BF_ERR_INVALID if the file cannot be opened.  Host only, no CUDA call. */
+bf_status bf_factor_file_check(const char *path, bf_desc *desc, int *dtype);
+
+/* bf_plan_create from a factor file (verified as by bf_factor_file_check
+ * before any CUDA call; the payload is read into a host buffer that is freed
+ * before returning).  Errors as bf_factor_file_check, then as bf_plan_create. */
+bf_status bf_plan_create_from_file(bf_plan *plan, const char *path, int nrhs_max, cudaStream_t stream);
+
+/* Running CRC-32 of `bytes` bytes (start from crc = 0), the checksum of the
+ * factor files. */
+unsigned int bf_crc32(const void *data, size_t bytes, unsigned int crc);
 
 /* Static text for a status code. */
 const char *bf_status_string(bf_status status);

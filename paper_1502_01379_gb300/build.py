@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libbfly.so")
-SOURCES = [os.path.join(CSRC, n) for n in ("bf_capi.cu", "bf_diff.cu", "bf_quad.cu", "bf_sketch.cu")]
+SOURCES = [os.path.join(CSRC, n) for n in ("bf_capi.cu", "bf_diff.cu", "bf_quad.cu", "bf_sketch.cu", "bf_file.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, n) for n in sorted(os.listdir(CSRC)) if n.endswith(".cuh")] + [
     os.path.join(INCLUDE, "bfly.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-BF_OK, BF_ERR_INVALID, BF_ERR_CUDA, BF_ERR_NOMEM, BF_ERR_UNSUPPORTED, BF_ERR_TIMEOUT = range(6)
+BF_OK, BF_ERR_INVALID, BF_ERR_CUDA, BF_ERR_NOMEM, BF_ERR_UNSUPPORTED, BF_ERR_TIMEOUT, BF_ERR_CORRUPT = range(7)
 BF_C64, BF_C128 = 1, 2
 
 EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", "bf_plan_check",
@@ -25,7 +25,8 @@ EXPORTS = ("bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_plan_destroy", 
            "bf_diff_saved_bytes", "bf_diff_forward", "bf_diff_backward", "bf_batch_create", "bf_batch_apply",
            "bf_batch_check", "bf_batch_items", "bf_batch_destroy", "bf_plan_set_precision", "bf_quad_create",
            "bf_quad_apply", "bf_quad_device_bytes", "bf_quad_passes", "bf_quad_destroy", "bf_quad_tc_passes",
-           "bf_quad_set_precision", "bf_quad_check", "bf_sketch_products")
+           "bf_quad_set_precision", "bf_quad_check", "bf_sketch_products", "bf_factor_file_check",
+           "bf_plan_create_from_file", "bf_crc32")
 BF_PREC_FP32, BF_PREC_TF32, BF_PREC_BF16X3, BF_PREC_BF16, BF_PREC_BF16X6 = 0, 1, 2, 3, 4
 BF_BATCH_EACH, BF_BATCH_GROUPED, BF_BATCH_GRAPH = 0, 1, 2
 
@@ -124,6 +125,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "bf_quad_set_precision": (i, [vp, i]),
         "bf_quad_check": (i, [vp, vp]),
         "bf_sketch_products": (i, [ctypes.POINTER(bf_sketch_desc), vp, vp, vp, vp]),
+        "bf_factor_file_check": (i, [ctypes.c_char_p, ctypes.POINTER(bf_desc), ctypes.POINTER(i)]),
+        "bf_plan_create_from_file": (i, [ctypes.POINTER(vp), ctypes.c_char_p, i, vp]),
+        "bf_crc32": (ctypes.c_uint, [vp, ctypes.c_size_t, ctypes.c_uint]),
         "bf_diff_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(bf_diff_desc)]),
         "bf_diff_destroy": (i, [vp]),
         "bf_diff_stride": (i, [vp]),
@@ -556,3 +560,62 @@ def bf_sketch_products(log2N: int, nb: int, blocks, out, lo: int, hi: int, node0
     _check(load().bf_sketch_products(ctypes.byref(d), ctypes.c_void_p(0 if c_fixed is None else c_fixed.data_ptr()),
                                      ctypes.c_void_p(blocks.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                      ctypes.c_void_p(_stream_handle(stream))), "bf_sketch_products")
+
+
+# ------------------------------------------------------------------ factor files
+FACTOR_FILE_VERSION = 1
+
+
+def bf_crc32(data: bytes, crc: int = 0) -> int:
+    """The library's CRC-32 (the factor files' checksum) of a bytes object."""
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    return int(load().bf_crc32(ctypes.cast(buf, ctypes.c_void_p), len(data), crc))
+
+
+def bf_factor_file_save(factors, path: str, dtype=np.complex64) -> int:
+    """Writes a factor file (the layout of include/bfly.h: 64-byte header with
+    magic, version, dtype, shape, payload size and CRC-32s; payload VL, H, S,
+    G, UL in canonical order) for `bf_plan_create_from_file`.  The checksum is
+    zlib's CRC-32, the same function as the library's.  Returns the bytes
+    written."""
+    import struct
+    import zlib
+    cdt = np.dtype(dtype)
+    if cdt not in (np.dtype(np.complex64), np.dtype(np.complex128)):
+        raise ValueError("dtype must be complex64 or complex128")
+    rdt = np.float32 if cdt == np.complex64 else np.float64
+    S = np.ascontiguousarray(factors.S, rdt).tobytes()
+    S += b"\0" * (-len(S) % 8)
+    parts = [np.ascontiguousarray(factors.VL, cdt)] + [np.ascontiguousarray(a, cdt) for a in factors.H] + \
+        [S] + [np.ascontiguousarray(a, cdt) for a in factors.G] + [np.ascontiguousarray(factors.UL, cdt)]
+    crc, size = 0, 0
+    for a in parts:
+        b = memoryview(a if isinstance(a, bytes) else a.reshape(-1).view(np.uint8))
+        crc = zlib.crc32(b, crc)
+        size += b.nbytes
+    head = b"BFLYFAC\0" + struct.pack("<IIiiiIQI", FACTOR_FILE_VERSION, BF_C64 if cdt == np.complex64 else BF_C128,
+                                      int(factors.L), int(factors.n0), int(factors.r), 0, size, crc)
+    head += struct.pack("<I", zlib.crc32(head)) + b"\0" * 16
+    with open(path, "wb") as f:
+        f.write(head)
+        for a in parts:
+            f.write(a if isinstance(a, bytes) else a.reshape(-1).view(np.uint8).data)
+    return len(head) + size
+
+
+def bf_factor_file_check(path: str):
+    """(L, leaf, r, dtype) of a verified factor file; raises BfError
+    (BF_ERR_CORRUPT, BF_ERR_UNSUPPORTED or BF_ERR_INVALID) otherwise."""
+    d = bf_desc()
+    dt = ctypes.c_int()
+    _check(load().bf_factor_file_check(os.fsencode(path), ctypes.byref(d), ctypes.byref(dt)), "bf_factor_file_check")
+    return d.L, d.leaf, d.r, dt.value
+
+
+def bf_plan_create_from_file(path: str, nrhs_max: int = 1, stream=None) -> Plan:
+    """A plan from a factor file (verified before any CUDA call)."""
+    L, leaf, r, _ = bf_factor_file_check(path)
+    h = ctypes.c_void_p()
+    _check(load().bf_plan_create_from_file(ctypes.byref(h), os.fsencode(path), int(nrhs_max),
+                                           ctypes.c_void_p(_stream_handle(stream))), "bf_plan_create_from_file")
+    return Plan(h.value, leaf << L, L, leaf, r, int(nrhs_max), _current_device())

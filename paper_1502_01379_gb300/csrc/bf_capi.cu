@@ -594,6 +594,7 @@ cudaError_t launch_wide(const bf_plan_s &P, const WideDirection &D, const float 
         p.slot_len = c.slot_len;
         for (int i = 0; i < wp.st.nlev; ++i) p.lev[i] = wp.st.lev[i];
         const dim3 grid((nrhs + NR - 1) / NR, P.m * wp.ngroups);
+        bfint::NvtxRange range(wp.down ? "bf_wide_kernel (merging pass)" : "bf_wide_kernel (splitting pass)");
         bfw::bf_wide_kernel<NR><<<grid, P.consumers + 32, smem, s>>>(p);
         if (tm && ps + 1 < np && !D.pass[ps + 1].down && wp.down) cudaEventRecord(tm->b, s);
     }
@@ -678,6 +679,7 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
             p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs) ? 1 : 0;
         const long long items = ntiles * P.m * wp.ngroups;
         const int grid = (int)std::min<long long>(items, P.num_sms);
+        bfint::NvtxRange range(wp.down ? "bf_tc_kernel (merging pass)" : "bf_tc_kernel (splitting pass)");
         if (p.bf16)
             bftc::bf_tc_kernel<true><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
         else
@@ -778,9 +780,15 @@ cudaError_t launch_pair(const bf_plan_s &P, const Direction &D, const float2 *in
     pu.S = D.d_S;
     pu.nrhs = nrhs;
     if (tm) cudaEventRecord(tm->a, s);
-    bfk::bf_down_kernel<T><<<grid, block, smem, s>>>(pd);
+    {
+        bfint::NvtxRange range("bf_down_kernel (leaf + merging levels)");
+        bfk::bf_down_kernel<T><<<grid, block, smem, s>>>(pd);
+    }
     if (tm) cudaEventRecord(tm->b, s);
-    bfk::bf_up_kernel<T><<<grid, block, smem, s>>>(pu);
+    {
+        bfint::NvtxRange range("bf_up_kernel (M^h + splitting levels + leaf)");
+        bfk::bf_up_kernel<T><<<grid, block, smem, s>>>(pu);
+    }
     if (tm) cudaEventRecord(tm->c, s);
     return cudaGetLastError();
 }
@@ -847,6 +855,7 @@ bf_status ensure_staging(bf_plan_s &P) {
 }
 
 bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cudaStream_t s, bool adjoint) {
+    bfint::NvtxRange range(adjoint ? "bf_apply_adjoint" : "bf_apply");
     if (!P || !in || !out || nrhs < 0 || ld < P->N) return BF_ERR_INVALID;
     if (nrhs == 0) return BF_OK;
     const char *ib = static_cast<const char *>(in);
@@ -1240,6 +1249,7 @@ bf_status bf_plan_kernel_times(bf_plan plan, int *down_launches, double *down_ms
 
 bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int nrhs, long long ld, int adjoint,
                                   cudaStream_t stream) {
+    bfint::NvtxRange range("bf_apply_static_scratch");
     bf_plan P = plan;
     if (!P || !in || !out || nrhs < 0 || ld < P->N) return BF_ERR_INVALID;
     if (P->R > kStaticScratchEntries) return BF_ERR_UNSUPPORTED;   // one vector's level-h data must fit
@@ -1276,6 +1286,7 @@ const char *bf_status_string(bf_status s) {
         case BF_ERR_NOMEM: return "BF_ERR_NOMEM: out of memory";
         case BF_ERR_UNSUPPORTED: return "BF_ERR_UNSUPPORTED: shape outside the library's compiled limits";
         case BF_ERR_TIMEOUT: return "BF_ERR_TIMEOUT: a kernel wait expired";
+        case BF_ERR_CORRUPT: return "BF_ERR_CORRUPT: a factor file failed its checks";
     }
     return "unknown bf_status";
 }
@@ -1431,6 +1442,7 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
 }
 
 bf_status bf_batch_apply(bf_batch B, int adjoint, int mode, cudaStream_t stream) {
+    bfint::NvtxRange range("bf_batch_apply");
     if (!B || mode < 0 || mode > 2) return BF_ERR_INVALID;
     const bool adj = adjoint != 0;
     if (mode == BF_BATCH_EACH) {   // one plan at a time: two launches per operator

@@ -39,6 +39,7 @@
 // segment from those checkpoints.  k = 1 keeps every level; the plan picks
 // k from a memory budget.
 #include "bfly.h"
+#include "bf_internal.h"
 
 #include <cuda_runtime.h>
 
@@ -470,6 +471,7 @@ size_t bf_diff_saved_bytes(bf_diff p, int nrhs) {
 
 bf_status bf_diff_forward(bf_diff p, const bf_dfactors *f, const void *g, void *u, int nrhs, long long ld,
                           void *saved, cudaStream_t s) {
+    bfint::NvtxRange range("bf_diff_forward");
     if (!p || !g || !u || !saved || nrhs < 1 || nrhs > p->nrhs_max || ld < p->N || !valid_factors(*p, f))
         return BF_ERR_INVALID;
     long long tot = 0;
@@ -492,6 +494,7 @@ bf_status bf_diff_forward(bf_diff p, const bf_dfactors *f, const void *g, void *
 
 bf_status bf_diff_backward(bf_diff p, const bf_dfactors *f, const void *ubar, void *gbar, int nrhs, long long ld,
                            const void *saved, const bf_dgrads *grads, cudaStream_t s) {
+    bfint::NvtxRange range("bf_diff_backward");
     if (!p || !ubar || !gbar || !saved || !grads || nrhs < 1 || nrhs > p->nrhs_max || ld < p->N ||
         !valid_factors(*p, f))
         return BF_ERR_INVALID;

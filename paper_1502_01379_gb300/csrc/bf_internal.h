@@ -2,9 +2,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>   // header-only NVTX v3: no library to link; a no-op without a tool attached
 #include <stdint.h>
 
 namespace bfint {
+
+// A named NVTX range for the lifetime of the object: profilers (Nsight
+// Systems, ncu's NVTX filters) show each entry point and kernel launch of the
+// library under its name.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // One level of a 2D (quadtree) factorization on the tensor-core core
 // (bf_tc.cuh, load/store kinds LD_QUAD / ST_QUAD): planar 128-RHS tiles of R

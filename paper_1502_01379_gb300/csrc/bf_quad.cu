@@ -560,6 +560,7 @@ bf_status bf_quad_create(bf_quad *out, const bf_desc *desc, const bf_factors *f,
 
 bf_status bf_quad_apply(bf_quad Q, const void *in, void *out, int nrhs, long long ld, int adjoint,
                         cudaStream_t stream) {
+    bfint::NvtxRange range(adjoint ? "bf_quad_apply (adjoint)" : "bf_quad_apply");
     if (!Q || nrhs < 0) return BF_ERR_INVALID;
     if (nrhs == 0) return BF_OK;
     if (!in || !out || ld < Q->N) return BF_ERR_INVALID;

@@ -20,7 +20,7 @@ def lib():
 
 def _declared(repo_root):
     text = open(os.path.join(repo_root, "include", "bfly.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:bf_status|size_t|int|const char \*)\s*(bf_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:bf_status|size_t|unsigned int|int|const char \*)\s*(bf_\w+)\s*\(", text, re.M)))
 
 
 def test_header_declares_the_abi(repo_root):
@@ -36,8 +36,9 @@ def test_library_exports_every_declared_symbol(lib, repo_root):
 
 
 def test_status_strings(lib):
-    for s in range(6):
+    for s in range(7):
         assert bf.bf_status_string(s).startswith("BF_")
+    assert "factor file" in bf.bf_status_string(capi.BF_ERR_CORRUPT)
 
 
 class _F:
@@ -150,3 +151,71 @@ def test_wrapper_passes_well_formed_buffers_to_the_library(lib):
         capi.bf_apply(P, x, y, nrhs=3, ld=P.N + 5, stream=0)
     assert not isinstance(e.value, capi.BfArgumentError)
     assert e.value.status == capi.BF_ERR_INVALID
+
+
+
+# ------------------------------------------------------------------ factor files
+def test_crc32_check_value_and_zlib_agree(lib):
+    """The CRC-32 of ISO-HDLC: check value 0xCBF43926 for "123456789" (its
+    published definition), and the library agrees with zlib on odd lengths
+    (the eight-bytes-per-step loop and the byte tail)."""
+    import zlib
+    assert capi.bf_crc32(b"123456789") == 0xCBF43926
+    rng = np.random.default_rng(0)
+    for n in (0, 1, 7, 8, 9, 63, 1000):
+        b = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        assert capi.bf_crc32(b) == zlib.crc32(b)
+        assert capi.bf_crc32(b[n // 2:], capi.bf_crc32(b[:n // 2])) == zlib.crc32(b)
+
+
+@pytest.mark.parametrize("L,n0,r,dtype", [(4, 4, 3, np.complex64), (0, 5, 3, np.complex64), (6, 2, 5, np.complex128)])
+def test_factor_file_round_trip_and_corruption(lib, tmp_path, L, n0, r, dtype):
+    """A saved factor file verifies and reports its shape; a flipped byte in
+    the payload or the header, a truncated or extended file, a wrong magic or
+    an inconsistent size field give BF_ERR_CORRUPT, another version
+    BF_ERR_UNSUPPORTED -- all before any CUDA call (no GPU here)."""
+    import struct
+    import zlib
+    from bfinputs import synthetic_factors
+    F = synthetic_factors(L, n0, r, seed=5, dtype=dtype)
+    path = str(tmp_path / "f.bfly")
+    nbytes = capi.bf_factor_file_save(F, path, dtype=dtype)
+    assert os.path.getsize(path) == nbytes
+    assert capi.bf_factor_file_check(path) == (L, n0, r, capi.BF_C64 if dtype == np.complex64 else capi.BF_C128)
+    good = open(path, "rb").read()
+    # the payload holds exactly the arrays in canonical order
+    pay = good[64:]
+    cdt = np.dtype(dtype)
+    assert np.array_equal(np.frombuffer(pay[:F.VL.size * cdt.itemsize], cdt).reshape(F.VL.shape), F.VL.astype(cdt))
+    assert np.array_equal(np.frombuffer(pay[-F.UL.size * cdt.itemsize:], cdt).reshape(F.UL.shape), F.UL.astype(cdt))
+
+    def check(blob):
+        bad = str(tmp_path / "bad.bfly")
+        open(bad, "wb").write(blob)
+        with pytest.raises(capi.BfError) as e:
+            capi.bf_factor_file_check(bad)
+        h = ctypes.c_void_p(7)
+        st = lib.bf_plan_create_from_file(ctypes.byref(h), os.fsencode(bad), 1, None)
+        assert st == e.value.status and h.value is None
+        return e.value.status
+
+    def rehead(blob, **kw):
+        fields = list(struct.unpack("<IIiiiIQI", blob[8:44]))
+        for k, v in kw.items():
+            fields[["version", "dtype", "L", "leaf", "r", "zero", "size", "crc"].index(k)] = v
+        head = blob[:8] + struct.pack("<IIiiiIQI", *fields)
+        return head + struct.pack("<I", zlib.crc32(head)) + blob[48:]
+
+    flip = lambda b, i: b[:i] + bytes([b[i] ^ 0x10]) + b[i + 1:]
+    assert check(flip(good, 64 + len(pay) // 2)) == capi.BF_ERR_CORRUPT        # payload byte
+    assert check(flip(good, len(good) - 1)) == capi.BF_ERR_CORRUPT              # last payload byte
+    assert check(flip(good, 18)) == capi.BF_ERR_CORRUPT                         # header byte (L)
+    assert check(good[:-8]) == capi.BF_ERR_CORRUPT                              # truncated
+    assert check(good + b"\0" * 8) == capi.BF_ERR_CORRUPT                       # trailing bytes
+    assert check(good[:40]) == capi.BF_ERR_CORRUPT                              # header cut
+    assert check(b"XFLYFAC\0" + good[8:]) == capi.BF_ERR_CORRUPT                # magic
+    assert check(rehead(good, size=len(pay) + 8)) == capi.BF_ERR_CORRUPT        # size field vs shape
+    assert check(rehead(good, r=33)) == capi.BF_ERR_CORRUPT                     # shape beyond limits
+    assert check(rehead(good, dtype=7)) == capi.BF_ERR_CORRUPT
+    assert check(rehead(good, version=2)) == capi.BF_ERR_UNSUPPORTED
+    assert lib.bf_factor_file_check(os.fsencode(str(tmp_path / "missing")), None, None) == capi.BF_ERR_INVALID

@@ -429,3 +429,27 @@ def test_tensor_core_bounded_waits_report_timeout(bf, monkeypatch):
     plan = bf.bf_plan_create(F, nrhs_max=128)
     assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
     plan.destroy()
+
+
+def test_plan_from_factor_file_matches_plan_from_arrays(bf, tmp_path):
+    """A factorization stored with bf_factor_file_save and planned with
+    bf_plan_create_from_file applies bit for bit like the plan made from the
+    arrays, in complex64 and complex128 files (complex128 input is rounded on
+    the device side exactly as bf_plan_create rounds it)."""
+    from bfinputs import complex_normal, synthetic_factors
+    from paper_1502_01379_gb300 import capi
+    for dtype in (np.complex64, np.complex128):
+        F = synthetic_factors(8, 16, 16, seed=21, dtype=dtype)
+        path = str(tmp_path / "f.bfly")
+        capi.bf_factor_file_save(F, path, dtype=dtype)
+        p1 = bf.bf_plan_create(F, nrhs_max=40)
+        p2 = capi.bf_plan_create_from_file(path, nrhs_max=40)
+        for n in (1, 40):
+            g = complex_normal((n, F.N), seed=n, dtype=np.complex64)
+            for adjoint in (False, True):
+                a = _run(bf, p1, g, adjoint=adjoint)
+                b = _run(bf, p2, g, adjoint=adjoint)
+                assert np.array_equal(a, b)
+                assert _rel(b, _oracle(F, g, adjoint)) < TOL
+        p1.destroy()
+        p2.destroy()
