@@ -430,6 +430,10 @@ def quad_line(dev, stream, name="fio2d_n65536_r24"):
         for kin, nout in ((4 * rk[lv + 1], 4 * rk[lv]), (4 * rk[lv], 4 * rk[lv + 1])):
             tc_mac += (s["nblocks"] // 4) * (2 * nout) * kin * 128 * 2 * ((nr + 127) // 128)
     useful = 8.0 * entries * nr
+    # bytes of one nr-vector apply: blocks once, then each level's output written
+    # and read by the next (lengths 4^L r_l between levels, N at the ends)
+    inner = [rk[lv] for lv in range(L - 1, L // 2 - 1, -1)] + [rk[lv + 1] for lv in range(L // 2, L - 1)]
+    quad_bytes = entries * 8 + nr * 8 * (2 * F.N + 2 * s["nblocks"] * sum(inner))
     tf32_peak, tf32_src = tf32_peak_tflops()
     rungs = {}
     for name, prec, products in (("fp32_3xtf32", capi.BF_PREC_FP32, 3), ("tf32", capi.BF_PREC_TF32, 1),
@@ -443,6 +447,10 @@ def quad_line(dev, stream, name="fio2d_n65536_r24"):
         ent = {"vectors_per_s": 2 * nr / (ms / 1e3), "ms_per_apply": ms / 2,
                "useful_tflops": useful / apply_s / 1e12,
                "rel_diff_vs_fp32_cuda_core": rel_diff(u, plain)}
+        ent["hbm"] = {"bound": "hbm", "achieved": quad_bytes / apply_s / 1e9, "peak": peak, "unit": "GB/s",
+                      "frac": quad_bytes / apply_s / 1e9 / peak, "peak_source": peak_src, "bytes": quad_bytes,
+                      "bytes_note": "per apply: every dense group block once + every level's input and output "
+                                    "(128-vector planar tiles between the levels, the caller's vectors at the ends)"}
         if prec in (capi.BF_PREC_FP32, capi.BF_PREC_TF32):
             issued = 2.0 * tc_mac * products        # 2 flops per multiply-add
             ent["roofline"] = {"bound": "tensor", "kernel": "bf_tc_kernel (inner levels)",
@@ -475,7 +483,8 @@ def batch_line(dev, stream):
            for i, m in enumerate(members)]
     outs = [torch.empty_like(x) for x in ins]
     nrhs = [m.nrhs for m in members]
-    cand = [(T, kb, st) for T in (1, 2, 4) for (kb, st) in ((16, 2), (64, 2))]
+    cand = [(T, kb, st) for T in (1, 2, 4) for (kb, st) in ((16, 2), (64, 2))] + \
+        [(4, 48, 3), (8, 32, 2), (8, 32, 3), (8, 48, 2)]
     cfg = B.autotune(Fs, ins, outs, nrhs, candidates=cand, reps=3)
     b = capi.bf_batch_create(Fs, ins, outs, nrhs, T=cfg["T"], slot_kb=cfg["slot_kb"], stages=cfg["stages"])
     vecs = 2 * sum(nrhs)                 # apply + adjoint of every operator's vectors
@@ -492,6 +501,27 @@ def batch_line(dev, stream):
         res["modes"][name] = {"ms_apply_plus_adjoint": ms, "vectors_per_s": vecs / (ms / 1e3)}
     res["graph_vs_each"] = res["modes"]["graph"]["vectors_per_s"] / res["modes"]["each"]["vectors_per_s"]
     b.destroy()
+    # HBM roofline of the graph mode (apply + adjoint): algorithmic bytes = every
+    # operator's factors once per direction + its vectors in and out; the
+    # grouped kernels stream an operator's factors once per RHS tile of T
+    # vectors, which the "streamed" figure counts
+    T = cfg["T"]
+    alg = streamed = 0
+    for F, n in zip(Fs, nrhs):
+        fb = factor_bytes(F)
+        vec = 2 * F.N * n * 8
+        alg += 2 * (fb + vec)
+        streamed += 2 * (fb * (-(-n // T)) + vec)
+    ms = res["modes"]["graph"]["ms_apply_plus_adjoint"]
+    peak, peak_src = load_peaks()
+    res["roofline"] = {"bound": "hbm", "kernel": "bf_grouped_down/up kernels (graph mode)",
+                       "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                       "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": peak_src,
+                       "alg_bytes": alg, "streamed_bytes": streamed,
+                       "streamed_gbs": streamed / (ms / 1e3) / 1e9,
+                       "bytes_note": "alg: per direction every operator's complex64 factors (leaves, transfer "
+                                     "levels, S) once + its vectors in and out; streamed: factors once per RHS "
+                                     f"tile of T={T} vectors, as the grouped kernels read them"}
     return res
 
 
@@ -617,6 +647,27 @@ def diff_line(dev, stream):
         dp.destroy()
         del saved
 
+    # Rooflines of the stride-1 forward + backward: bytes = factors read by the
+    # forward and by the backward, gradients written (the factors' size),
+    # kept inputs written and read back, the four vectors; flops = three
+    # passes of complex multiply-adds per RHS (forward, input gradient, factor
+    # gradients), on FP32 CUDA cores
+    fb = factor_bytes(F)
+    kept = res["strides"]["1"]["saved_mb"] * 1e6
+    alg = 3 * fb + 2 * kept + 4 * F.N * nrhs * 8
+    flops = 3 * 8.0 * apply_macs(F) * nrhs
+    secs = res["strides"]["1"]["forward_backward_ms"] / 1e3
+    peak, peak_src = load_peaks()
+    fpeak = fp32_fma_peak_tflops(dev)
+    res["roofline"] = {"bound": "hbm", "kernel": "bf_diff unit kernels (stride 1)",
+                       "achieved": alg / secs / 1e9, "peak": peak, "unit": "GB/s",
+                       "frac": alg / secs / 1e9 / peak, "peak_source": peak_src, "alg_bytes": alg,
+                       "fp32_tflops": flops / secs / 1e12, "fp32_peak_tflops": fpeak,
+                       "fp32_frac": flops / secs / 1e12 / fpeak,
+                       "bytes_note": "3 x complex64 factor bytes (forward read, backward read, gradient write) "
+                                     "+ 2 x kept factor inputs + 4 vectors; flops: 3 x 8 per complex multiply-add "
+                                     "per RHS"}
+
     def rel(a, b):
         a, b = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128)
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -649,6 +700,14 @@ def tf32_peak_tflops():
             return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
     except Exception:
         return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
+
+
+def factor_bytes(F):
+    """Bytes of one direction's complex64 factors: two leaf factors (2^L
+    blocks n0 x r), 2h transfer levels (2^L blocks r x 2r) and S (m^2 r
+    floats)."""
+    nb = 1 << F.L
+    return 8 * apply_macs(F) + 4 * F.m * F.m * F.r
 
 
 def apply_macs(F):

@@ -184,7 +184,7 @@ bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int n
 typedef struct bf_batch_s *bf_batch;
 
 typedef struct {
-    int T;          /* RHS per thread block: 1, 2 or 4 (0 = 1)                      */
+    int T;          /* RHS per thread block: 1, 2, 4 or 8 (0 = 1)                   */
     int slot_kb;    /* factor ring slot size in KB (0 = 16)                          */
     int stages;     /* ring slots (0 = 2)                                            */
 } bf_batch_config;

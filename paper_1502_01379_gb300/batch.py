@@ -5,7 +5,7 @@ A batch applies many factorizations of uneven size, rank and vector count
 together (bf_batch_* in libbfly.so): one grouped launch runs every
 operator's down half, a second every up half, and the pair is captured once
 into a CUDA graph.  What the grouped kernels can vary is the RHS tile per
-thread block (T = 1, 2, 4) and the factor ring (slot size, slots): bigger
+thread block (T = 1, 2, 4, 8) and the factor ring (slot size, slots): bigger
 tiles reuse each factor entry more, smaller rings let more thread blocks
 share an SM.  `autotune` times each candidate on the actual batch (CUDA
 events, the graph mode), keeps the fastest, and caches the choice on disk,
@@ -21,7 +21,8 @@ import tempfile
 from . import capi
 
 # (T, slot_kb, stages)
-CANDIDATES = [(T, kb, st) for T in (1, 2, 4) for (kb, st) in ((8, 2), (16, 2), (32, 2), (64, 2), (16, 3))]
+CANDIDATES = [(T, kb, st) for T in (1, 2, 4, 8) for (kb, st) in ((8, 2), (16, 2), (32, 2), (64, 2), (16, 3))] + \
+    [(4, 48, 3), (8, 32, 3), (8, 48, 2)]
 
 
 def default_cache_path() -> str:

@@ -1323,8 +1323,10 @@ cudaError_t launch_grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
 }
 
 cudaError_t grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
-    return B.T == 4 ? launch_grouped<4>(B, adjoint, s) : B.T == 2 ? launch_grouped<2>(B, adjoint, s)
-                                                                  : launch_grouped<1>(B, adjoint, s);
+    return B.T == 8   ? launch_grouped<8>(B, adjoint, s)
+         : B.T == 4 ? launch_grouped<4>(B, adjoint, s)
+         : B.T == 2 ? launch_grouped<2>(B, adjoint, s)
+                    : launch_grouped<1>(B, adjoint, s);
 }
 
 template <int T>
@@ -1360,7 +1362,7 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
     *out = nullptr;
     if (n < 1 || !descs || !factors || !in || !outv || !nrhs || !ld) return BF_ERR_INVALID;
     const int T = cfg && cfg->T ? cfg->T : 1;
-    if (T != 1 && T != 2 && T != 4) return BF_ERR_INVALID;
+    if (T != 1 && T != 2 && T != 4 && T != 8) return BF_ERR_INVALID;
     for (int o = 0; o < n; ++o) {
         if (!in[o] || !outv[o] || nrhs[o] < 1 || nrhs[o] > descs[o].nrhs_max) return BF_ERR_INVALID;
         if (ld[o] < ((long long)descs[o].leaf << descs[o].L)) return BF_ERR_INVALID;
@@ -1424,7 +1426,10 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
     }
     B->nitems = (int)items.size();
     bf_status st = BF_OK;
-    st = T == 4 ? set_grouped_attr<4>(B->smem) : T == 2 ? set_grouped_attr<2>(B->smem) : set_grouped_attr<1>(B->smem);
+    st = T == 8   ? set_grouped_attr<8>(B->smem)
+       : T == 4 ? set_grouped_attr<4>(B->smem)
+       : T == 2 ? set_grouped_attr<2>(B->smem)
+                : set_grouped_attr<1>(B->smem);
     if (st != BF_OK) {
         free_batch(B);
         return st;

@@ -497,13 +497,15 @@ __global__ void __launch_bounds__(288, 1) bf_up_kernel(const Params p) {
 // Grouped launches: many operators (each its own Params) in one grid.  CTA i
 // runs work item items[i] = (operator, node, RHS tile) with that operator's
 // Params, copied to shared memory first.  Register-bounded for two CTAs per
-// SM: batches are mostly small operators whose CTAs need little shared memory.
+// SM up to 4 RHS per tile (batches are mostly small operators whose CTAs need
+// little shared memory); 8-RHS tiles hold 8 vectors of a node segment (up to
+// 128 KB) and take one CTA per SM.
 struct GroupItem {
     int op, node, rhs0, pad_;
 };
 
 template <int T>
-__global__ void __launch_bounds__(288, 2) bf_down_grouped(const Params *plist, const GroupItem *items) {
+__global__ void __launch_bounds__(288, (T >= 8 ? 1 : 2)) bf_down_grouped(const Params *plist, const GroupItem *items) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Params sp;
     const GroupItem it = items[blockIdx.x];
@@ -513,7 +515,7 @@ __global__ void __launch_bounds__(288, 2) bf_down_grouped(const Params *plist, c
 }
 
 template <int T>
-__global__ void __launch_bounds__(288, 2) bf_up_grouped(const Params *plist, const GroupItem *items) {
+__global__ void __launch_bounds__(288, (T >= 8 ? 1 : 2)) bf_up_grouped(const Params *plist, const GroupItem *items) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Params sp;
     const GroupItem it = items[blockIdx.x];

@@ -42,7 +42,7 @@ def _batch_inputs(shapes, seed):
     return Fs, gs
 
 
-@pytest.mark.parametrize("T", [1, 2, 4])
+@pytest.mark.parametrize("T", [1, 2, 4, 8])
 def test_mixed_batch_all_modes_against_oracle(bf, T):
     from oracle import apply as A
     from paper_1502_01379_gb300 import capi
