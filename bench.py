@@ -305,6 +305,17 @@ def run_ours(args, rank, world, local):
                 "note": "useful = 8 real flops per complex multiply-add of the factored operator; issued = "
                         "the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi, Re and Im accumulators) of the dense per-group "
                         "blocks; TF32 peak = measured bf16 dense peak x 1.1/2.25 (nominal TF32/BF16)"}
+            # HBM: the passes' own traffic (by construction) and the fully fused
+            # bound (factors once + the vectors in and out, no intermediate)
+            own = tc_traffic_bytes(F, n)
+            fused = factor_bytes(F) + 2 * N * n * 8
+            peak, peak_src = load_peaks()
+            ent["tensor"]["hbm"] = {
+                "bound": "hbm", "achieved": own / apply_s / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": own / apply_s / 1e9 / peak, "peak_source": peak_src, "traffic_bytes": own,
+                "fused_bytes": fused, "frac_of_fused_bound": fused / apply_s / 1e9 / peak,
+                "note": "traffic_bytes: every pass's dense blocks + the pass intermediates written and read + "
+                        "the vectors (2-level passes); fused_bytes: a schedule keeping every intermediate on chip"}
         if n == 128 and "tensor" in ent:
             # precision ladder of the tensor-core core: the other rungs beside 3xTF32,
             # each compared with the FP32 CUDA-core fused path on vector 0
@@ -747,6 +758,28 @@ def tc_issued_flops(F, nrhs):
             items = F.m * (F.m >> kb) * ntiles
             total += items * 6 * (kin // 8) * 2 * 128 * (2 * nout) * 8
     return total
+
+
+def tc_traffic_bytes(F, nrhs):
+    """HBM bytes one tensor-core apply moves by construction: every pass reads
+    its dense [Re F; Im F] blocks once per 128-RHS tile, the first pass reads
+    the caller's vectors, the last writes them, and each of the passes - 1
+    intermediates (R = 2^L r positions x 128-RHS tiles, complex64) is written
+    once and read once."""
+    kmax = _tc_group_bits(F.n0, F.r)
+    chunks = [(a, min(kmax, F.h - a)) for a in range(0, F.h, kmax)] or [(0, 0)]
+    ntiles = -(-nrhs // 128)
+    blocks, passes = 0, 0
+    for half in (0, 1):
+        seq = chunks if half == 0 else chunks[::-1]
+        for i, (a, kb) in enumerate(seq):
+            G = 1 << kb
+            kin = G * (F.n0 if (half == 0 and i == 0) else F.r)
+            nout = G * (F.n0 if (half == 1 and i == len(seq) - 1) else F.r)
+            blocks += F.m * (F.m >> kb) * ntiles * 2 * nout * kin * 4
+            passes += 1
+    R = (1 << F.L) * F.r
+    return blocks + 8 * nrhs * (2 * F.N + 2 * R * (passes - 1))
 
 
 def load_traffic(kernel_name):

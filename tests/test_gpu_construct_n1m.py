@@ -145,6 +145,19 @@ def test_dft_n1m_against_fft_closed_form(bf, L, n0, r):
     assert eo <= 10 * eps and eoa <= 10 * eps
     if L == 18:
         assert eps < 1e-5 and eo < 1e-5                              # an accurate factorization
+    # 32 vectors through the multi-RHS cores on the same factors (the tensor-core
+    # core at leaf 16; the CUDA-core core at leaf 4, which the tensor cores do not
+    # take): every column against the single-vector path and the FFT
+    plan = bf.bf_plan_create(F, nrhs_max=32)
+    G32 = complex_normal((32, N), seed=13, dtype=np.complex64)
+    G32[:2] = g
+    U32 = _gpu_apply(bf, plan, G32)
+    A32 = _gpu_apply(bf, plan, G32, adjoint=True)
+    plan.destroy()
+    assert _rel(U32[:2], u) < TOL and _rel(A32[:2], a) < TOL
+    for j in (0, 5, 31):
+        assert _rel(U32[j], KK.dft_closed_form(G32[j], N)) <= 10 * eps + TOL
+        assert _rel(A32[j], np.fft.fft(sign * G32[j].astype(np.complex128))) <= 10 * eps + TOL
 
 
 @pytest.mark.parametrize("L,n0,r", [(16, 16, 16), (18, 4, 16)])
