@@ -125,7 +125,11 @@ bf_status bf_apply_adjoint(bf_plan plan, const void *in, void *out, int nrhs, lo
 bf_status bf_plan_destroy(bf_plan plan);
 
 /* Reads and clears the plan's device error word (synchronizes `stream`):
- * BF_ERR_TIMEOUT if a kernel gave up on a bounded wait since the last check. */
+ * BF_ERR_TIMEOUT if a kernel gave up on a bounded wait since the last check.
+ * In the checked build of the library (libbfly_checked.so, compiled with
+ * BF_CHECKED: the single-vector and batched kernels test every global index
+ * against the extent their launch's arguments define, skip an access outside
+ * it and record it): BF_ERR_INVALID if such a check fired. */
 bf_status bf_plan_check(bf_plan plan, cudaStream_t stream);
 
 /* Bytes of device memory the plan holds (factors, workspace, staging). */

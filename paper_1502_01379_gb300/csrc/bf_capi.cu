@@ -747,6 +747,8 @@ Params base_params(const bf_plan_s &P, const Stream &st) {
     std::memset(&p, 0, sizeof(p));
     p.fac = st.d;
     p.cta_len = st.cta_len;
+    p.fac_elems = (long long)P.m * st.cta_len;
+    p.s_elems = (long long)P.m * P.m * P.r;
     p.err = P.d_err;
     p.stall = P.inject_stall;
     p.nlev = st.nlev;
@@ -772,6 +774,8 @@ cudaError_t launch_pair(const bf_plan_s &P, const Direction &D, const float2 *in
     pd.out = P.d_ws;
     pd.ld_out = P.R;
     pd.nrhs = nrhs;
+    pd.in_elems = (long long)(nrhs - 1) * ld_in + P.N;
+    pd.out_elems = P.R * ws_rhs(P);
     Params pu = base_params(P, D.up);
     pu.in = P.d_ws;
     pu.ld_in = P.R;
@@ -779,6 +783,13 @@ cudaError_t launch_pair(const bf_plan_s &P, const Direction &D, const float2 *in
     pu.ld_out = ld_out;
     pu.S = D.d_S;
     pu.nrhs = nrhs;
+    pu.in_elems = P.R * ws_rhs(P);
+    pu.out_elems = (long long)(nrhs - 1) * ld_out + P.N;
+#ifdef BF_CHECKED
+    // test hook of the checked build: state the output one element short, so the
+    // kernel's last store falls outside and must be skipped and reported
+    if (env_int("BF_CHECKED_SHRINK_OUT", 0) == 1) pu.out_elems -= 1;
+#endif
     if (tm) cudaEventRecord(tm->a, s);
     {
         bfint::NvtxRange range("bf_down_kernel (leaf + merging levels)");
@@ -1003,6 +1014,8 @@ cudaError_t launch_pair_static(const bf_plan_s &P, const Direction &D, const flo
     pd.out = ws;
     pd.ld_out = P.R;
     pd.nrhs = nrhs;
+    pd.in_elems = (long long)(nrhs - 1) * ld_in + P.N;
+    pd.out_elems = kStaticScratchEntries;
     Params pu = base_params(P, D.up);
     pu.in = ws;
     pu.ld_in = P.R;
@@ -1010,6 +1023,8 @@ cudaError_t launch_pair_static(const bf_plan_s &P, const Direction &D, const flo
     pu.ld_out = ld_out;
     pu.S = D.d_S;
     pu.nrhs = nrhs;
+    pu.in_elems = kStaticScratchEntries;
+    pu.out_elems = (long long)(nrhs - 1) * ld_out + P.N;
     bfk::bf_down_kernel<T><<<grid, block, smem, s>>>(pd);
     bfk::bf_up_kernel<T><<<grid, block, smem, s>>>(pu);
     return cudaGetLastError();
@@ -1216,7 +1231,7 @@ bf_status bf_plan_check(bf_plan plan, cudaStream_t stream) {
     if (h) {
         BF_CUDA(cudaMemsetAsync(plan->d_err, 0, sizeof(unsigned), stream));
         BF_CUDA(cudaStreamSynchronize(stream));
-        return BF_ERR_TIMEOUT;
+        return (h & bfk::kErrBounds) ? BF_ERR_INVALID : BF_ERR_TIMEOUT;   // bounds: checked builds only
     }
     return BF_OK;
 }
@@ -1402,6 +1417,8 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
             pd.out = P->d_ws;
             pd.ld_out = P->R;
             pd.nrhs = nrhs[o];
+            pd.in_elems = (long long)(nrhs[o] - 1) * ld[o] + P->N;
+            pd.out_elems = P->R * ws_rhs(*P);
             Params pu = base_params(*P, D.up);
             pu.in = P->d_ws;
             pu.ld_in = P->R;
@@ -1409,6 +1426,8 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
             pu.ld_out = ld[o];
             pu.S = D.d_S;
             pu.nrhs = nrhs[o];
+            pu.in_elems = P->R * ws_rhs(*P);
+            pu.out_elems = (long long)(nrhs[o] - 1) * ld[o] + P->N;
             host[(size_t)(2 * dir) * n + o] = pd;
             host[(size_t)(2 * dir + 1) * n + o] = pu;
         }

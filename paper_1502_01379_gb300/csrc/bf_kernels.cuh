@@ -68,8 +68,26 @@ struct Params {
     int stages;             // ring depth
     int slot_len;           // complex elements per ring slot
     int stall;              // failure-detection test hook: the producer issues no copies
+    // Extents (elements) of the buffers behind fac, in, out and S: what the launch's
+    // arguments define.  Checked builds (BF_CHECKED) test every global index against
+    // them; other builds ignore them.
+    long long fac_elems, in_elems, out_elems, s_elems;
     Level lev[kMaxLevels];
 };
+
+// Checked builds: a global index outside its buffer's extent sets kErrBounds
+// in the error word and the access is skipped (a load reads zero), so a
+// kernel indexing mistake shows up as a status instead of a memory fault.
+constexpr unsigned kErrBounds = 2u;
+#ifdef BF_CHECKED
+__device__ __forceinline__ bool in_extent(unsigned *err, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(err, kErrBounds);
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_extent(unsigned *, long long, long long) { return true; }
+#endif
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -137,6 +155,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 // --------------------------------------------------------------- producer
 // One thread streams this CTA's factor chunk, stage by stage, into the ring.
 // Streams one factor chunk (all levels of one CTA work item) into the ring;
+// Extent of a producer's factor stream (checked builds; parameter types
+// without one are not checked).
+__device__ __forceinline__ long long fac_extent(const Params &p) { return p.fac_elems; }
+template <class P>
+__device__ __forceinline__ long long fac_extent(const P &) { return 1LL << 62; }
+
 // `gs` counts stages across calls.  Returns false if a wait gave up.
 template <class P>
 __device__ __forceinline__ bool produce_chunk(const P &p, long long chunk, uint32_t &gs, float2 *ring, uint64_t *full,
@@ -149,6 +173,10 @@ __device__ __forceinline__ bool produce_chunk(const P &p, long long chunk, uint3
             const uint32_t use = gs / p.stages;
             if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, abort_flag, p.err)) return false;
             const uint32_t bytes = (uint32_t)lv.stage_len * 8u;
+            if (!in_extent(p.err, (long long)(src - p.fac) + lv.stage_len - 1, fac_extent(p))) {
+                *abort_flag = 1;   // consumers stop waiting; nothing is copied
+                return false;
+            }
             mbar_arrive_expect_tx(&full[slot], bytes);
             bulk_g2s(ring + (long long)slot * p.slot_len, src, bytes, &full[slot]);
             src += lv.stage_len;
@@ -338,7 +366,10 @@ __device__ __forceinline__ void store_row(const Params &p, const Level &lv, floa
         const long long o = (long long)node * p.n0 * p.m + obase + rr;
 #pragma unroll
         for (int t = 0; t < T; ++t)
-            if (t < nt) p.out[(long long)(rhs0 + t) * p.ld_out + o] = a.get(t);
+            if (t < nt) {
+                const long long i = (long long)(rhs0 + t) * p.ld_out + o;
+                if (in_extent(p.err, i, p.out_elems)) p.out[i] = a.get(t);
+            }
     }
 }
 
@@ -437,7 +468,8 @@ __device__ __forceinline__ void down_body(const Params &p, unsigned char *smem_r
         const long long base = (long long)node * nin;
         for (int e = tid; e < nin * T; e += nconsumers) {
             const int t = e % T, ee = e / T;
-            s.buf0[e] = (t < nt) ? __ldg(p.in + (long long)(rhs0 + t) * p.ld_in + base + ee) : make_float2(0.f, 0.f);
+            const long long i = (long long)(rhs0 + t) * p.ld_in + base + ee;
+            s.buf0[e] = (t < nt && in_extent(p.err, i, p.in_elems)) ? __ldg(p.in + i) : make_float2(0.f, 0.f);
         }
         consumer_sync(nconsumers);
         const float2 *res = run_levels<T>(p, s, nconsumers, node, rhs0, nt);
@@ -446,7 +478,10 @@ __device__ __forceinline__ void down_body(const Params &p, unsigned char *smem_r
         const long long obase = (long long)node * nseg;
         for (int e = tid; e < nseg * T; e += nconsumers) {
             const int t = e % T, ee = e / T;
-            if (t < nt) p.out[(long long)(rhs0 + t) * p.ld_out + obase + ee] = res[e];
+            if (t < nt) {
+                const long long i = (long long)(rhs0 + t) * p.ld_out + obase + ee;
+                if (in_extent(p.err, i, p.out_elems)) p.out[i] = res[e];
+            }
         }
     }
     __syncthreads();
@@ -470,9 +505,13 @@ __device__ __forceinline__ void up_body(const Params &p, unsigned char *smem_raw
             const int q = ee / p.r, k = ee - q * p.r;
             float2 v = make_float2(0.f, 0.f);
             if (t < nt) {
-                const float w = __ldg(p.S + (long long)node * nseg + ee);
-                const float2 x = __ldg(p.in + (long long)(rhs0 + t) * p.ld_in + ((long long)q * p.m + node) * p.r + k);
-                v = make_float2(w * x.x, w * x.y);
+                const long long is = (long long)node * nseg + ee;
+                const long long ix = (long long)(rhs0 + t) * p.ld_in + ((long long)q * p.m + node) * p.r + k;
+                if (in_extent(p.err, is, p.s_elems) && in_extent(p.err, ix, p.in_elems)) {
+                    const float w = __ldg(p.S + is);
+                    const float2 x = __ldg(p.in + ix);
+                    v = make_float2(w * x.x, w * x.y);
+                }
             }
             s.buf0[e] = v;
         }
