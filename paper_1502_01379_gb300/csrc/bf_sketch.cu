@@ -15,8 +15,8 @@
 // computed by the caller) and |xi_k|.  The sum is rounded to 24 bits (2^-25
 // turn, 1.9e-7 rad) and sin / cos taken in FP32 (sincospif).
 //
-// Layout: one thread per output index o (a row x for the forward products, a
-// column xi for the adjoint ones), 128 per CTA; blockIdx.y is the sketch
+// Layout: two output indices o per thread (rows x for the forward products,
+// columns xi for the adjoint ones), 256 per CTA; blockIdx.y is the sketch
 // block (node); the node's nb summation indices stream through shared memory
 // in chunks of 64 together with the block's rows (broadcast reads: every
 // thread of the CTA reads the same entry), each thread accumulating k complex
@@ -39,30 +39,43 @@ struct Args {
     int log2N, nb, k, node0;
 };
 
+// Two outputs per thread (o and o + TPB): each staged sketch entry feeds both
+// from one shared-memory load, halving the loads per multiply-add.
+constexpr int ROWS = 2;
+
 template <int KP, bool ADJ>
 __global__ void __launch_bounds__(TPB) sketch_kernel(Args a) {
     __shared__ float2 sb[SCHUNK][KP];
     __shared__ unsigned long long sc[SCHUNK];
-    const long long o = a.lo + (long long)blockIdx.x * TPB + threadIdx.x;
-    const bool valid = o < a.hi;
     const int b = blockIdx.y;
     const long long s0 = (long long)(a.node0 + b) * a.nb;
     const float2 *blk = a.blocks + (long long)b * a.nb * a.k;
     const int sh = 64 - a.log2N;
     const long long half = 1LL << (a.log2N - 1);
-    // per-thread phase constants
-    unsigned long long mul = 0, cx = 0, axi = 0;
-    if (!ADJ) {
-        mul = (unsigned long long)(valid ? o : 0) << sh;                 // x << sh, times xi' below
-        cx = (a.c && valid) ? a.c[o] : 0ULL;
-    } else {
-        const long long xi = (valid ? o : 0) - half;
-        mul = (unsigned long long)xi << sh;                              // xi' << sh, times x below
-        axi = (unsigned long long)(xi < 0 ? -xi : xi);
-    }
-    float2 acc[KP];
+    long long o[ROWS];
+    bool valid[ROWS];
+    unsigned long long mul[ROWS], cx[ROWS], axi[ROWS];
 #pragma unroll
-    for (int c = 0; c < KP; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int q = 0; q < ROWS; ++q) {
+        o[q] = a.lo + (long long)blockIdx.x * (TPB * ROWS) + q * TPB + threadIdx.x;
+        valid[q] = o[q] < a.hi;
+        const long long oo = valid[q] ? o[q] : 0;
+        if (!ADJ) {
+            mul[q] = (unsigned long long)oo << sh;                    // x << sh, times xi' below
+            cx[q] = (a.c && valid[q]) ? a.c[oo] : 0ULL;
+            axi[q] = 0;
+        } else {
+            const long long xi = oo - half;
+            mul[q] = (unsigned long long)xi << sh;                    // xi' << sh, times x below
+            axi[q] = (unsigned long long)(xi < 0 ? -xi : xi);
+            cx[q] = 0;
+        }
+    }
+    float2 acc[ROWS][KP];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q)
+#pragma unroll
+        for (int c = 0; c < KP; ++c) acc[q][c] = make_float2(0.f, 0.f);
     for (int t0 = 0; t0 < a.nb; t0 += SCHUNK) {
         const int tn = min(SCHUNK, a.nb - t0);
         __syncthreads();
@@ -75,38 +88,46 @@ __global__ void __launch_bounds__(TPB) sketch_kernel(Args a) {
         __syncthreads();
         for (int t = 0; t < tn; ++t) {
             const long long s = s0 + t0 + t;
-            unsigned long long P;
-            if (!ADJ) {
-                const long long xi = s - half;
-                P = mul * (unsigned long long)xi + cx * (unsigned long long)(xi < 0 ? -xi : xi);
-            } else {
-                P = (unsigned long long)s * mul + sc[t] * axi;
+            float sn[ROWS], cs[ROWS];
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q) {
+                unsigned long long P;
+                if (!ADJ) {
+                    const long long xi = s - half;
+                    P = mul[q] * (unsigned long long)xi + cx[q] * (unsigned long long)(xi < 0 ? -xi : xi);
+                } else {
+                    P = (unsigned long long)s * mul[q] + sc[t] * axi[q];
+                }
+                // 2 frac(Phi) in [0, 2), rounded to 24 bits (a wrap to 2^24 is 2 = 0 turns)
+                const unsigned w = (unsigned)(((P + (1ULL << 39)) >> 40) & 0xFFFFFFULL);
+                sincospif((float)w * (1.0f / 8388608.0f), &sn[q], &cs[q]);
+                if (ADJ) sn[q] = -sn[q];                                  // conj(K)
             }
-            // 2 frac(Phi) in [0, 2), rounded to 24 bits (a wrap to 2^24 is 2 = 0 turns)
-            const unsigned q = (unsigned)(((P + (1ULL << 39)) >> 40) & 0xFFFFFFULL);
-            float sn, cs;
-            sincospif((float)q * (1.0f / 8388608.0f), &sn, &cs);
-            if (ADJ) sn = -sn;                                           // conj(K)
 #pragma unroll
             for (int c = 0; c < KP; ++c) {
                 const float2 v = sb[t][c];
-                acc[c].x = fmaf(cs, v.x, fmaf(-sn, v.y, acc[c].x));
-                acc[c].y = fmaf(cs, v.y, fmaf(sn, v.x, acc[c].y));
+#pragma unroll
+                for (int q = 0; q < ROWS; ++q) {
+                    acc[q][c].x = fmaf(cs[q], v.x, fmaf(-sn[q], v.y, acc[q][c].x));
+                    acc[q][c].y = fmaf(cs[q], v.y, fmaf(sn[q], v.x, acc[q][c].y));
+                }
             }
         }
     }
-    if (valid) {
-        const long long rows = a.hi - a.lo;
-        float2 *dst = a.out + (long long)b * a.k * rows + (o - a.lo);
+    const long long rows = a.hi - a.lo;
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        if (!valid[q]) continue;
+        float2 *dst = a.out + (long long)b * a.k * rows + (o[q] - a.lo);
 #pragma unroll
         for (int c = 0; c < KP; ++c)
-            if (c < a.k) dst[(long long)c * rows] = acc[c];
+            if (c < a.k) dst[(long long)c * rows] = acc[q][c];
     }
 }
 
 template <int KP>
 cudaError_t launch(const Args &a, int nodes, bool adjoint, cudaStream_t s) {
-    const dim3 grid((unsigned)((a.hi - a.lo + TPB - 1) / TPB), (unsigned)nodes);
+    const dim3 grid((unsigned)((a.hi - a.lo + TPB * ROWS - 1) / (TPB * ROWS)), (unsigned)nodes);
     if (adjoint)
         sketch_kernel<KP, true><<<grid, TPB, 0, s>>>(a);
     else
@@ -147,8 +168,12 @@ extern "C" bf_status bf_sketch_products(const bf_sketch_desc *d, const unsigned 
     a.k = d->k;
     a.node0 = d->node0;
     const bool adj = d->adjoint != 0;
+    // exact widths for k = r + 5 at r = 8, 12, 16 (the construction's sketches), else padded
     cudaError_t e = d->k <= 8    ? bfs::launch<8>(a, d->nodes, adj, stream)
+                  : d->k == 13 ? bfs::launch<13>(a, d->nodes, adj, stream)
                   : d->k <= 16 ? bfs::launch<16>(a, d->nodes, adj, stream)
+                  : d->k == 17 ? bfs::launch<17>(a, d->nodes, adj, stream)
+                  : d->k == 21 ? bfs::launch<21>(a, d->nodes, adj, stream)
                   : d->k <= 24 ? bfs::launch<24>(a, d->nodes, adj, stream)
                                : bfs::launch<32>(a, d->nodes, adj, stream);
     if (e != cudaSuccess) {
