@@ -886,7 +886,11 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         float2 *dst = static_cast<float2 *>(out) + (long long)c0 * ld;
         long long ld_in = ld, ld_out = ld;
         if (host_in) {
-            BF_CUDA(cudaMemcpy2DAsync(P->d_stage_in, P->N * 8, src, ld * 8, P->N * 8, nc, cudaMemcpyHostToDevice, s));
+            if (ld == P->N)   // contiguous columns: one plain copy
+                BF_CUDA(cudaMemcpyAsync(P->d_stage_in, src, (size_t)nc * P->N * 8, cudaMemcpyHostToDevice, s));
+            else
+                BF_CUDA(cudaMemcpy2DAsync(P->d_stage_in, P->N * 8, src, ld * 8, P->N * 8, nc, cudaMemcpyHostToDevice,
+                                          s));
             src = P->d_stage_in;
             ld_in = P->N;
         }
@@ -931,8 +935,13 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
                        : launch_pair<1>(*P, D, src, ld_in, kdst, ld_out, nc, s, tm);
         }
         if (e != cudaSuccess) return cuda_fail(e);
-        if (host_out)
-            BF_CUDA(cudaMemcpy2DAsync(dst, ld * 8, P->d_stage_out, P->N * 8, P->N * 8, nc, cudaMemcpyDeviceToHost, s));
+        if (host_out) {
+            if (ld == P->N)
+                BF_CUDA(cudaMemcpyAsync(dst, P->d_stage_out, (size_t)nc * P->N * 8, cudaMemcpyDeviceToHost, s));
+            else
+                BF_CUDA(cudaMemcpy2DAsync(dst, ld * 8, P->d_stage_out, P->N * 8, P->N * 8, nc, cudaMemcpyDeviceToHost,
+                                          s));
+        }
     }
     return BF_OK;
 }
