@@ -86,6 +86,20 @@ __device__ __forceinline__ void cadd(float2 &a, float2 b) {
     a.x += b.x;
     a.y += b.y;
 }
+// y += x * z, y += conj(x) * z, y += x * conj(z): four FMAs each.
+__device__ __forceinline__ void cmac(float2 &y, float2 x, float2 z) {
+    y.x = fmaf(x.x, z.x, fmaf(-x.y, z.y, y.x));
+    y.y = fmaf(x.x, z.y, fmaf(x.y, z.x, y.y));
+}
+__device__ __forceinline__ void cmac_conj_a(float2 &y, float2 x, float2 z) {
+    y.x = fmaf(x.x, z.x, fmaf(x.y, z.y, y.x));
+    y.y = fmaf(x.x, z.y, fmaf(-x.y, z.x, y.y));
+}
+__device__ __forceinline__ void cmac_conj_b(float2 &y, float2 x, float2 z) {
+    y.x = fmaf(x.x, z.x, fmaf(x.y, z.y, y.x));
+    y.y = fmaf(x.y, z.x, fmaf(-x.x, z.y, y.y));
+}
+constexpr int kTile = 4;   // outputs per warp lane in the step loops (register tile)
 
 // One CTA per unit; RHS in chunks of kChunk.  Shared memory: the unit's
 // parameter blocks, its P-side chunk (count p rows) and Q-side chunk (q rows).
@@ -126,18 +140,47 @@ __global__ void __launch_bounds__(kThreads) unit_kernel(const Unit a) {
                 Qs[o * kPad + lane] = lane < nc ? qv[pos * a.nrhs + j0 + lane] : make_float2(0.f, 0.f);
             }
         __syncthreads();
+        // Each lane is one RHS; a warp takes kTile consecutive outputs at a time
+        // (fewer when there are too few to give every warp kTile), so each
+        // shared-memory value of the lane's vector feeds kTile multiply-adds.
         if (a.form == FORM_XH) {   // Q[o][j] = sum_c sum_row conj(X_c[row][o]) P_c[row][j]
-            for (int o = warp; o < a.q; o += kThreads / 32) {
-                float2 y = make_float2(0.f, 0.f);
-                for (int rr = 0; rr < np; ++rr) cadd(y, cmul_conj_a(Xs[rr * a.q + o], Ps[rr * kPad + lane]));
-                if (lane < nc) a.dst[((size_t)u * a.q + o) * a.nrhs + j0 + lane] = y;
+            const int tile = max(1, min(kTile, a.q / (kThreads / 32)));
+            for (int ob = warp * tile; ob < a.q; ob += tile * (kThreads / 32)) {
+                float2 y[kTile];
+#pragma unroll
+                for (int i = 0; i < kTile; ++i) y[i] = make_float2(0.f, 0.f);
+                for (int rr = 0; rr < np; ++rr) {
+                    const float2 pv = Ps[rr * kPad + lane];
+                    const float2 *xr = Xs + rr * a.q + ob;
+#pragma unroll
+                    for (int i = 0; i < kTile; ++i)
+                        if (i < tile && ob + i < a.q) cmac_conj_a(y[i], xr[i], pv);
+                }
+#pragma unroll
+                for (int i = 0; i < kTile; ++i)
+                    if (i < tile && ob + i < a.q && lane < nc)
+                        a.dst[((size_t)u * a.q + ob + i) * a.nrhs + j0 + lane] = y[i];
             }
         } else {                   // P_c[row][j] = sum_o X_c[row][o] Q[o][j]
-            for (int rr = warp; rr < np; rr += kThreads / 32) {
-                float2 y = make_float2(0.f, 0.f);
-                for (int o = 0; o < a.q; ++o) cadd(y, cmul(Xs[rr * a.q + o], Qs[o * kPad + lane]));
-                const int c = rr / a.p, row = rr - c * a.p;
-                if (lane < nc) a.dst[((size_t)p_block(a, u, c) * a.p + row) * a.nrhs + j0 + lane] = y;
+            const int tile = max(1, min(kTile, np / (kThreads / 32)));
+            for (int rb = warp * tile; rb < np; rb += tile * (kThreads / 32)) {
+                float2 y[kTile];
+#pragma unroll
+                for (int i = 0; i < kTile; ++i) y[i] = make_float2(0.f, 0.f);
+                for (int o = 0; o < a.q; ++o) {
+                    const float2 qv = Qs[o * kPad + lane];
+#pragma unroll
+                    for (int i = 0; i < kTile; ++i)
+                        if (i < tile && rb + i < np) cmac(y[i], Xs[(rb + i) * a.q + o], qv);
+                }
+#pragma unroll
+                for (int i = 0; i < kTile; ++i) {
+                    const int rr = rb + i;
+                    if (i < tile && rr < np && lane < nc) {
+                        const int c = rr / a.p, row = rr - c * a.p;
+                        a.dst[((size_t)p_block(a, u, c) * a.p + row) * a.nrhs + j0 + lane] = y[i];
+                    }
+                }
             }
         }
         if (grad) {                // Xbar_c[row][o] += sum_j P_c[row][j] conj(Q[o][j])
@@ -148,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) unit_kernel(const Unit a) {
                     const int rr = e / a.q, o = e - rr * a.q;
                     const float2 *pr = Ps + rr * kPad, *qr = Qs + o * kPad;
                     float2 s = acc[t];
-                    for (int j = 0; j < nc; ++j) cadd(s, cmul_conj_b(pr[j], qr[j]));
+                    for (int j = 0; j < nc; ++j) cmac_conj_b(s, pr[j], qr[j]);
                     acc[t] = s;
                 }
             }
