@@ -453,3 +453,25 @@ def test_plan_from_factor_file_matches_plan_from_arrays(bf, tmp_path):
                 assert _rel(b, _oracle(F, g, adjoint)) < TOL
         p1.destroy()
         p2.destroy()
+
+
+def test_largest_node_segment_leaf64_r32_n1m(bf):
+    """The compiled limits at once: L = 14, leaf 64, rank 32 (N = 2^20), a
+    middle-level node segment of m max(leaf, r) = 8192 entries (the largest a
+    plan takes; its ring slots shrink to fit shared memory).  Every output
+    entry of the apply and the adjoint, one vector on the fused kernels and
+    9 vectors on the multi-RHS core, against the FP64 C loops of the oracle."""
+    from bfinputs import complex_normal, synthetic_factors
+    from oracle import capply
+    F = synthetic_factors(14, 64, 32, seed=41, dtype=np.complex64)
+    assert F.m * max(F.n0, F.r) == 8192
+    P = capply.PreparedFactors(F)
+    for nrhs in (1, 9):
+        plan = bf.bf_plan_create(F, nrhs_max=nrhs)
+        g = complex_normal((nrhs, F.N), seed=nrhs, dtype=np.complex64)
+        u = _run(bf, plan, g)
+        a = _run(bf, plan, g, adjoint=True)
+        plan.destroy()
+        for j in sorted({0, nrhs - 1}):
+            assert _rel(u[j], capply.bf_apply_c(P, g[j])) < TOL
+            assert _rel(a[j], capply.bf_adjoint_c(P, g[j])) < TOL
