@@ -518,11 +518,17 @@ def batch_line(dev, stream):
     # vectors, which the "streamed" figure counts
     T = cfg["T"]
     alg = streamed = 0
+    routed = 0
     for F, n in zip(Fs, nrhs):
         fb = factor_bytes(F)
         vec = 2 * F.N * n * 8
         alg += 2 * (fb + vec)
-        streamed += 2 * (fb * (-(-n // T)) + vec)
+        if n >= 8 and F.L >= 6:     # routed to its own multi-RHS passes: factors once, 3 intermediates
+            routed += 1
+            streamed += 2 * (fb + vec + 2 * 3 * (1 << F.L) * F.r * n * 8)
+        else:
+            streamed += 2 * (fb * (-(-n // T)) + vec)
+    res["routed_operators"] = routed
     ms = res["modes"]["graph"]["ms_apply_plus_adjoint"]
     peak, peak_src = load_peaks()
     res["roofline"] = {"bound": "hbm", "kernel": "bf_grouped_down/up kernels (graph mode)",
@@ -532,7 +538,8 @@ def batch_line(dev, stream):
                        "streamed_gbs": streamed / (ms / 1e3) / 1e9,
                        "bytes_note": "alg: per direction every operator's complex64 factors (leaves, transfer "
                                      "levels, S) once + its vectors in and out; streamed: factors once per RHS "
-                                     f"tile of T={T} vectors, as the grouped kernels read them"}
+                                     f"tile of T={T} vectors for the grouped operators, once for the routed ones "
+                                     "(>= 8 vectors, L >= 6) plus their pass intermediates"}
     return res
 
 

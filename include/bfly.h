@@ -183,14 +183,22 @@ bf_status bf_apply_static_scratch(bf_plan plan, const void *in, void *out, int n
  * operator, middle-level node and RHS tile, largest operators first), then
  * every up half in a second, optionally replayed from a CUDA graph.  Each
  * operator is the fused path of bf_apply with its own factors, packed with
- * the batch's ring configuration.
+ * the batch's ring configuration.  Operators with many vectors on deep trees
+ * (nrhs >= route_min_rhs and L >= route_min_L) are routed instead to their
+ * own CUDA-core multi-RHS passes (as bf_apply runs 8 or more vectors), which
+ * read each factor once per direction instead of once per RHS tile; those
+ * passes run on eight side streams beside the grouped launches (forked from
+ * and joined back into the caller's stream, inside the graph too).
  * ------------------------------------------------------------------------- */
 typedef struct bf_batch_s *bf_batch;
 
 typedef struct {
-    int T;          /* RHS per thread block: 1, 2, 4 or 8 (0 = 1)                   */
-    int slot_kb;    /* factor ring slot size in KB (0 = 16)                          */
-    int stages;     /* ring slots (0 = 2)                                            */
+    int T;              /* RHS per thread block: 1, 2, 4 or 8 (0 = 1)                  */
+    int slot_kb;        /* factor ring slot size in KB (0 = 16)                         */
+    int stages;         /* ring slots (0 = 2)                                           */
+    int route_min_rhs;  /* route operators with at least this many vectors (0 = 8;      */
+                        /* negative: route none)                                        */
+    int route_min_L;    /* ... and trees at least this deep (0 = 6)                     */
 } bf_batch_config;
 
 typedef enum {

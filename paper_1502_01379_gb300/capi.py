@@ -65,7 +65,8 @@ bf_dgrads = bf_dfactors   # same shape: device pointers (written by the backward
 
 
 class bf_batch_config(ctypes.Structure):
-    _fields_ = [("T", ctypes.c_int), ("slot_kb", ctypes.c_int), ("stages", ctypes.c_int)]
+    _fields_ = [("T", ctypes.c_int), ("slot_kb", ctypes.c_int), ("stages", ctypes.c_int),
+                ("route_min_rhs", ctypes.c_int), ("route_min_L", ctypes.c_int)]
 
 
 class bf_sketch_desc(ctypes.Structure):
@@ -496,9 +497,11 @@ class Batch:
 
 
 def bf_batch_create(factors_list, ins, outs, nrhs, T: int = 1, slot_kb: int = 0, stages: int = 0,
-                    stream=None) -> Batch:
+                    route_min_rhs: int = 0, route_min_L: int = 0, stream=None) -> Batch:
     """A batch of operators (factors in canonical layout, host arrays) bound to
-    device vectors ins[o], outs[o] of shape (nrhs[o], N_o) complex64."""
+    device vectors ins[o], outs[o] of shape (nrhs[o], N_o) complex64.
+    Operators with at least ``route_min_rhs`` vectors (0: 8; negative: none)
+    and depth at least ``route_min_L`` (0: 6) run their own multi-RHS passes."""
     n = len(factors_list)
     descs = (bf_desc * n)()
     facs = (bf_factors * n)()
@@ -512,7 +515,7 @@ def bf_batch_create(factors_list, ins, outs, nrhs, T: int = 1, slot_kb: int = 0,
     out_arr = (ctypes.c_void_p * n)(*[_addr(x) for x in outs])
     nr = (ctypes.c_int * n)(*[int(x) for x in nrhs])
     lds = (ctypes.c_longlong * n)(*[int(F.n0) << int(F.L) for F in factors_list])
-    cfg = bf_batch_config(int(T), int(slot_kb), int(stages))
+    cfg = bf_batch_config(int(T), int(slot_kb), int(stages), int(route_min_rhs), int(route_min_L))
     h = ctypes.c_void_p()
     _check(load().bf_batch_create(ctypes.byref(h), n, descs, facs, in_arr, out_arr, nr, lds, ctypes.byref(cfg),
                                   ctypes.c_void_p(_stream_handle(stream))), "bf_batch_create")

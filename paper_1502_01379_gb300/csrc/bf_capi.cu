@@ -1054,6 +1054,8 @@ struct PlanCfg {
     int stages = 3;
     size_t smem_limit = kMaxSmem;
     bool fused_only = false;   // no multi-RHS cores (grouped batches use the fused kernels)
+    bool no_tc = false;        // no tensor-core core (routed batch operators use the CUDA-core one)
+    int wide_min = 0;          // smallest batch for the CUDA-core core (0: BF_WIDE_MIN, default 8)
 };
 
 PlanCfg env_plan_cfg() {
@@ -1144,7 +1146,7 @@ bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, c
     // and every pass's dense blocks fit the core; each call uses it for
     // batches of at least tc_min (measured on GB300 at N = 2^20, r = 16: from
     // 32 RHS on, 128-RHS work items beat the CUDA-core core even part-filled).
-    P->wide_min = cfg.fused_only ? (1 << 30) : env_int("BF_WIDE_MIN", 8);
+    P->wide_min = cfg.fused_only ? (1 << 30) : cfg.wide_min > 0 ? cfg.wide_min : env_int("BF_WIDE_MIN", 8);
     P->tc_min = cfg.fused_only ? (1 << 30) : env_int("BF_TC_MIN", 32);
     if (P->nrhs_max >= P->wide_min) {
         WideCfg c;
@@ -1167,7 +1169,7 @@ bf_status create_plan(bf_plan *plan, const bf_desc *desc, const bf_factors *f, c
             make_wide_passes(P->wadj, *P, c);
         }
     }
-    if (P->nrhs_max >= std::max(P->tc_min, 1) && env_int("BF_TC", 1) == 1) {
+    if (P->nrhs_max >= std::max(P->tc_min, 1) && env_int("BF_TC", 1) == 1 && !cfg.no_tc) {
         // Groups of G = 4 slots (two levels per pass) when the dense blocks fit
         // (G max(n0, r) <= 64), else G = 2 or 1; BF_TC_KMAX caps the slot bits.
         int kb = 2;
@@ -1334,6 +1336,10 @@ struct bf_batch_s {
     std::vector<long long> ld;
     cudaStream_t cap = nullptr;           // private stream for graph capture
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<int> routed;              // operators on their own multi-RHS passes
+    static constexpr int kSide = 8;       // side streams for the routed operators (4 measured the same)
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
 };
 
 namespace {
@@ -1346,11 +1352,43 @@ cudaError_t launch_grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
+cudaError_t grouped_only(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
+    if (B.nitems == 0) return cudaSuccess;
     return B.T == 8   ? launch_grouped<8>(B, adjoint, s)
          : B.T == 4 ? launch_grouped<4>(B, adjoint, s)
          : B.T == 2 ? launch_grouped<2>(B, adjoint, s)
                     : launch_grouped<1>(B, adjoint, s);
+}
+
+// One routed operator: its plan's CUDA-core multi-RHS passes on its vectors.
+cudaError_t launch_routed(const bf_batch_s &B, int o, bool adjoint, cudaStream_t s) {
+    const bf_plan_s &P = *B.plans[o];
+    const WideDirection &WD = adjoint ? P.wadj : P.wfwd;
+    const Direction &D = adjoint ? P.adj : P.fwd;
+    const int nc = B.nrhs[o];
+    const float2 *in = static_cast<const float2 *>(B.in[o]);
+    float2 *out = static_cast<float2 *>(B.out[o]);
+    const int NR = std::min(WD.cfg.nr_max, nc <= 16 ? 16 : nc <= 32 ? 32 : 64);
+    return NR == 64 ? launch_wide<64>(P, WD, D.d_S, in, B.ld[o], out, B.ld[o], nc, s, nullptr)
+         : NR == 32 ? launch_wide<32>(P, WD, D.d_S, in, B.ld[o], out, B.ld[o], nc, s, nullptr)
+                    : launch_wide<16>(P, WD, D.d_S, in, B.ld[o], out, B.ld[o], nc, s, nullptr);
+}
+
+// The whole batch on stream s: the routed operators' passes on the side
+// streams (forked from s first, joined back at the end) beside the grouped
+// launches on s.  Usable under stream capture.
+cudaError_t grouped(const bf_batch_s &B, bool adjoint, cudaStream_t s) {
+    if (B.routed.empty()) return grouped_only(B, adjoint, s);
+    cudaError_t e = cudaEventRecord(B.fork, s);
+    for (int k = 0; k < bf_batch_s::kSide && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(B.side[k], B.fork, 0);
+    if (e == cudaSuccess) e = grouped_only(B, adjoint, s);
+    for (size_t i = 0; i < B.routed.size() && e == cudaSuccess; ++i)
+        e = launch_routed(B, B.routed[i], adjoint, B.side[i % bf_batch_s::kSide]);
+    for (int k = 0; k < bf_batch_s::kSide && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(B.join[k], B.side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, B.join[k], 0);
+    }
+    return e;
 }
 
 template <int T>
@@ -1368,6 +1406,11 @@ void free_batch(bf_batch_s *B) {
     for (auto &e : B->exec)
         if (e) cudaGraphExecDestroy(e);
     if (B->cap) cudaStreamDestroy(B->cap);
+    for (int k = 0; k < bf_batch_s::kSide; ++k) {
+        if (B->side[k]) cudaStreamDestroy(B->side[k]);
+        if (B->join[k]) cudaEventDestroy(B->join[k]);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
     cudaFree(B->d_params);
     cudaFree(B->d_items);
     for (bf_plan p : B->plans) free_plan(p);
@@ -1402,17 +1445,39 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
     pc.stages = cfg && cfg->stages ? cfg->stages : 2;
     pc.fused_only = true;
     pc.smem_limit = kMaxSmem - 2048;   // the grouped kernels' Params copy is static shared memory
+    const int route_rhs = cfg && cfg->route_min_rhs ? cfg->route_min_rhs : 8;
+    const int route_L = cfg && cfg->route_min_L ? cfg->route_min_L : 6;
     std::vector<Params> host(4 * (size_t)n);
     std::vector<bfk::GroupItem> items;
     std::vector<std::pair<long long, int>> order;   // (work, operator)
     for (int o = 0; o < n; ++o) {
         bf_plan P = nullptr;
-        bf_status st = create_plan(&P, &descs[o], &factors[o], stream, pc);
+        const bool route = route_rhs > 0 && nrhs[o] >= route_rhs && descs[o].L >= route_L;
+        bf_status st = BF_OK;
+        if (route) {   // its own plan with the CUDA-core multi-RHS core (no tensor-core blocks)
+            PlanCfg rc;
+            rc.no_tc = true;
+            rc.wide_min = route_rhs;
+            st = create_plan(&P, &descs[o], &factors[o], stream, rc);
+            if (st == BF_OK && !P->wide) {   // the core does not take this shape: back to the group
+                free_plan(P);
+                P = nullptr;
+            }
+        }
+        if (!P && st == BF_OK) st = create_plan(&P, &descs[o], &factors[o], stream, pc);
         if (st != BF_OK) {
             free_batch(B);
             return st;
         }
         B->plans.push_back(P);
+        B->in.push_back(in[o]);
+        B->out.push_back(outv[o]);
+        B->nrhs.push_back(nrhs[o]);
+        B->ld.push_back(ld[o]);
+        if (P->wide) {
+            B->routed.push_back(o);
+            continue;
+        }
         if (plan_smem(*P, T) > pc.smem_limit) {
             free_batch(B);
             return BF_ERR_UNSUPPORTED;
@@ -1441,10 +1506,16 @@ bf_status bf_batch_create(bf_batch *out, int n, const bf_desc *descs, const bf_f
             host[(size_t)(2 * dir + 1) * n + o] = pu;
         }
         order.push_back({(long long)P->m * ((nrhs[o] + T - 1) / T) * (P->fwd.down.cta_len + P->fwd.up.cta_len), o});
-        B->in.push_back(in[o]);
-        B->out.push_back(outv[o]);
-        B->nrhs.push_back(nrhs[o]);
-        B->ld.push_back(ld[o]);
+    }
+    if (!B->routed.empty()) {
+        bool ok = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < bf_batch_s::kSide && ok; ++k)
+            ok = cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&B->join[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            free_batch(B);
+            return cuda_fail(cudaErrorUnknown);
+        }
     }
     std::sort(order.begin(), order.end(), [](auto &a, auto &b) { return a.first > b.first; });
     for (auto &w : order) {

@@ -42,14 +42,18 @@ def _batch_inputs(shapes, seed):
     return Fs, gs
 
 
-@pytest.mark.parametrize("T", [1, 2, 4, 8])
-def test_mixed_batch_all_modes_against_oracle(bf, T):
+@pytest.mark.parametrize("T,route", [(1, None), (2, None), (4, None), (8, None), (2, (4, 4)), (4, (2, 2))])
+def test_mixed_batch_all_modes_against_oracle(bf, T, route):
+    """route = (route_min_rhs, route_min_L): operators with that many vectors on
+    trees that deep run their own CUDA-core multi-RHS passes on side streams
+    beside the grouped launches (None: the defaults, which route none of these)."""
     from oracle import apply as A
     from paper_1502_01379_gb300 import capi
     Fs, gs = _batch_inputs(MIXED, seed=900 + T)
     ins = [torch.from_numpy(g).cuda() for g in gs]
     outs = [torch.empty_like(x) for x in ins]
-    b = capi.bf_batch_create(Fs, ins, outs, [g.shape[0] for g in gs], T=T)
+    kw = {} if route is None else dict(route_min_rhs=route[0], route_min_L=route[1])
+    b = capi.bf_batch_create(Fs, ins, outs, [g.shape[0] for g in gs], T=T, **kw)
     assert capi.bf_batch_items(b) > 0
     results = {}
     for adjoint in (False, True):
