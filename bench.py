@@ -558,7 +558,9 @@ def construction_line(dev, stream, log2N=18, L=16, r=16):
     from bfinputs import complex_normal
     N = 1 << log2N
     res = {"workload": f"construction from sketch products: DFT and 1D FIO (Example 1), N=2^{log2N}, L={L}, "
-                       f"leaf={N >> L}, r={r}, p=5; FP32 products, FP64 decompositions"}
+                       f"leaf={N >> L}, r={r}, p=5; FP32 products, FP64 decompositions (libraries warmed up "
+                       "by an untimed N=2^10 construction first)"}
+    construct.construct_kernel_1d("dft", 1 << 10, 6, 8, seed=1)      # first use of cuSOLVER / cuBLAS, untimed
     for kind in ("dft", "fio"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
