@@ -750,13 +750,13 @@ def tc_eligible(F):
 
 
 def tc_issued_flops(F, nrhs):
-    """Tensor-core flops one apply issues: per pass, every (node, group, 128-RHS
+    """Tensor-core flops one apply issues: per pass, every (node, group, RHS
     tile) item runs 6 Kin/8 MMAs of 128 x 2 Nout x 8 (the same pass split as
     the library: chunks of up to two slot bits, leaf folded into the first down
-    and the last up pass)."""
+    and the last up pass); a tile narrower than 128 RHS still issues M = 128."""
     kmax = _tc_group_bits(F.n0, F.r)
     chunks = [(a, min(kmax, F.h - a)) for a in range(0, F.h, kmax)] or [(0, 0)]
-    ntiles = -(-nrhs // 128)
+    ntiles = -(-nrhs // tc_tile_width(nrhs))
     total = 0
     for half in (0, 1):
         seq = chunks if half == 0 else chunks[::-1]
@@ -769,15 +769,24 @@ def tc_issued_flops(F, nrhs):
     return total
 
 
+def tc_tile_width(nrhs):
+    """RHS per tile of the tensor-core core for a call of nrhs vectors (as the
+    library picks it): the fewest tiles of at most 128, evened out and rounded
+    up to a multiple of 32."""
+    ntiles = -(-nrhs // 128)
+    return min(128, -(-(-(-nrhs // ntiles)) // 32) * 32)
+
+
 def tc_traffic_bytes(F, nrhs):
     """HBM bytes one tensor-core apply moves by construction: every pass reads
-    its dense [Re F; Im F] blocks once per 128-RHS tile, the first pass reads
+    its dense [Re F; Im F] blocks once per RHS tile, the first pass reads
     the caller's vectors, the last writes them, and each of the passes - 1
-    intermediates (R = 2^L r positions x 128-RHS tiles, complex64) is written
-    once and read once."""
+    intermediates (R = 2^L r positions x the tiles' W columns each, complex64)
+    is written once and read once."""
     kmax = _tc_group_bits(F.n0, F.r)
     chunks = [(a, min(kmax, F.h - a)) for a in range(0, F.h, kmax)] or [(0, 0)]
-    ntiles = -(-nrhs // 128)
+    W = tc_tile_width(nrhs)
+    ntiles = -(-nrhs // W)
     blocks, passes = 0, 0
     for half in (0, 1):
         seq = chunks if half == 0 else chunks[::-1]
@@ -788,7 +797,7 @@ def tc_traffic_bytes(F, nrhs):
             blocks += F.m * (F.m >> kb) * ntiles * 2 * nout * kin * 4
             passes += 1
     R = (1 << F.L) * F.r
-    return blocks + 8 * nrhs * (2 * F.N + 2 * R * (passes - 1))
+    return blocks + 8 * nrhs * 2 * F.N + 8 * ntiles * W * 2 * R * (passes - 1)
 
 
 def load_traffic(kernel_name):

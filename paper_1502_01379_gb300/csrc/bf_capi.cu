@@ -17,6 +17,10 @@
 #include <utility>
 #include <vector>
 
+namespace bfint {
+cudaError_t tc_launch(const bftc::TcParams &p, int grid, cudaStream_t s);
+}
+
 namespace {
 
 using bfk::Level;
@@ -622,29 +626,39 @@ EncodeTiledFn encode_tiled_fn() {
 }
 
 // Tensor map of nrhs column-major vectors (16-byte aligned, even ld) as a
-// {2 N floats, nrhs rows} FP32 tensor read in tiles of 32 floats x 128 rows
+// {2 N floats, nrhs rows} FP32 tensor read in tiles of 32 floats x W rows
 // with the 128-byte swizzle; false if it cannot be made.
-bool points_tmap(CUtensorMap *map, const float2 *in, long long N, long long ld, int nrhs) {
+bool points_tmap(CUtensorMap *map, const float2 *in, long long N, long long ld, int nrhs, int W) {
     EncodeTiledFn fn = encode_tiled_fn();
     if (!fn) return false;
     const cuuint64_t dim[2] = {(cuuint64_t)(2 * N), (cuuint64_t)nrhs};
     const cuuint64_t stride[1] = {(cuuint64_t)ld * 8};
-    const cuuint32_t box[2] = {32, (cuuint32_t)bftc::NR};
+    const cuuint32_t box[2] = {32, (cuuint32_t)W};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(in), dim, stride, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// RHS per tile of a tensor-core apply of nrhs vectors: the fewest tiles of at
+// most 128, evened out and rounded up to a multiple of 32 (one warp's lanes),
+// so a call with fewer than 128 vectors moves only the columns it uses.
+int tc_tile_width(int nrhs) {
+    const int ntiles = (nrhs + bftc::NR - 1) / bftc::NR;
+    const int per = (nrhs + ntiles - 1) / ntiles;
+    return std::min(bftc::NR, (per + 31) / 32 * 32);
+}
+
 // Tensor-core multi-RHS core: one persistent launch (one CTA per SM) per
-// pass; pass intermediates are 128-RHS tiles, position-major and planar
-// ([tile][position][re 128 | im 128]).  `in` / `out` must be 16-byte aligned
-// with an even leading dimension.
+// pass; pass intermediates are W-RHS tiles, position-major and planar
+// ([tile][position][re W | im W], W = tc_tile_width(nrhs)).  `in` / `out`
+// must be 16-byte aligned with an even leading dimension.
 cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *in, long long ld_in, float2 *out,
                       long long ld_out, int nrhs, cudaStream_t s, Timing *tm) {
     float2 *buf[2] = {P.d_wsA, P.d_ws};
     const int np = (int)D.pass.size();
-    const long long ntiles = (nrhs + bftc::NR - 1) / bftc::NR;
+    const int W = tc_tile_width(nrhs);
+    const long long ntiles = (nrhs + W - 1) / W;
     if (tm) cudaEventRecord(tm->a, s);
     for (int ps = 0; ps < np; ++ps) {
         const WidePass &wp = D.pass[ps];
@@ -672,18 +686,16 @@ cudaError_t launch_tc(const bf_plan_s &P, const WideDirection &D, const float2 *
         p.Kin = wp.Kin;
         p.Nout = wp.Nout;
         p.nrhs = nrhs;
+        p.W = W;
         p.split = P.tc_split;
         p.bf16 = P.tc_bf16;
         p.stall = P.inject_stall;
         if (p.load_kind == bftc::LD_POINTS && env_int("BF_TC_TMAP", 1) == 1)
-            p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs) ? 1 : 0;
+            p.use_tmap = points_tmap(&p.tmap, p.in, P.N, p.ld_in, nrhs, W) ? 1 : 0;
         const long long items = ntiles * P.m * wp.ngroups;
         const int grid = (int)std::min<long long>(items, P.num_sms);
         bfint::NvtxRange range(wp.down ? "bf_tc_kernel (merging pass)" : "bf_tc_kernel (splitting pass)");
-        if (p.bf16)
-            bftc::bf_tc_kernel<true><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
-        else
-            bftc::bf_tc_kernel<false><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
+        bfint::tc_launch(p, grid, s);
         if (tm && ps + 1 < np && !D.pass[ps + 1].down && wp.down) cudaEventRecord(tm->b, s);
     }
     if (tm) cudaEventRecord(tm->c, s);
@@ -1671,12 +1683,34 @@ bf_status bf_batch_destroy(bf_batch B) {
 
 namespace bfint {
 
-cudaError_t tc_prepare() {
-    const cudaError_t e = cudaFuncSetAttribute(bftc::bf_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)bftc::kSmemBytes);
+template <int EPI>
+cudaError_t tc_prepare_epi() {
+    const cudaError_t e = cudaFuncSetAttribute(bftc::bf_tc_kernel<false, EPI>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bftc::Epi<EPI>::smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(bftc::bf_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bftc::kSmemBytes);
+    return cudaFuncSetAttribute(bftc::bf_tc_kernel<true, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bftc::Epi<EPI>::smem);
+}
+
+cudaError_t tc_prepare() {
+    const cudaError_t e = tc_prepare_epi<8>();
+    return e != cudaSuccess ? e : tc_prepare_epi<16>();
+}
+
+// One tensor-core pass: 16 epilogue warps for tiles of up to 96 RHS, 8 for 128.
+cudaError_t tc_launch(const bftc::TcParams &p, int grid, cudaStream_t s) {
+    if (p.W <= 96) {
+        if (p.bf16)
+            bftc::bf_tc_kernel<true, 16><<<grid, bftc::Epi<16>::threads, bftc::Epi<16>::smem, s>>>(p);
+        else
+            bftc::bf_tc_kernel<false, 16><<<grid, bftc::Epi<16>::threads, bftc::Epi<16>::smem, s>>>(p);
+    } else {
+        if (p.bf16)
+            bftc::bf_tc_kernel<true, 8><<<grid, bftc::Epi<8>::threads, bftc::Epi<8>::smem, s>>>(p);
+        else
+            bftc::bf_tc_kernel<false, 8><<<grid, bftc::Epi<8>::threads, bftc::Epi<8>::smem, s>>>(p);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
@@ -1695,6 +1729,7 @@ cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
     p.Kin = q.Kin;
     p.Nout = q.Nout;
     p.nrhs = q.nrhs;
+    p.W = bftc::NR;   // the 2D CUDA-core edge levels read and write 128-wide planar tiles
     p.split = q.split;
     p.bf16 = q.bf16;
     p.stall = q.stall;
@@ -1713,11 +1748,7 @@ cudaError_t quad_tc_launch(const QuadTc &q, int num_sms, cudaStream_t s) {
     const long long ntiles = (q.nrhs + bftc::NR - 1) / bftc::NR;
     const long long items = (long long)q.ngroups * q.parts * ntiles;
     const int grid = (int)std::min<long long>(items, num_sms);
-    if (p.bf16)
-            bftc::bf_tc_kernel<true><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
-        else
-            bftc::bf_tc_kernel<false><<<grid, bftc::kThreads, bftc::kSmemBytes, s>>>(p);
-    return cudaGetLastError();
+    return tc_launch(p, grid, s);
 }
 
 cudaError_t bf16_split(const float *fac, uint16_t *out, long long nblocks, int rows, int Kin, int parts,

@@ -12,9 +12,11 @@
 // diagonal S^h of M^h (Eq. KeqUMV) into the first up pass.  The host forms
 // these products in FP64 when the plan is created; each pass of the apply is
 // then one dense complex block per (node, group of G <= 4 slots) applied to
-// 128 RHS at a time:  Y = F X with F of Nout x Kin (Nout, Kin <= 64).
+// a tile of W <= 128 RHS at a time:  Y = F X with F of Nout x Kin (Nout,
+// Kin <= 64).
 //
-// Tensor-core mapping.  The RHS sit on the MMA M dimension (M = 128): the
+// Tensor-core mapping.  The RHS sit on the MMA M dimension (M = 128; rows
+// W .. 127 of a narrower tile are never read out): the
 // activation tile X (128 RHS x Kin) is the A operand, read from tensor
 // memory, and the block F is the B operand, streamed by TMA into shared
 // memory as one K-major operand [Re F; Im F] of 2 Nout rows.  Two real
@@ -50,17 +52,21 @@
 // part needs Kin/2 <= 32 columns; the three-way split keeps X_mid in the
 // upper 32 columns of the X_hi range.
 //
-// Pass intermediates are 128-RHS tiles stored position-major and planar:
-// position pos of tile t holds the 128 real parts, then the 128 imaginary
-// parts (1 KB), so an r-block is one contiguous copy and each warp access to
-// one part of one position is 128 contiguous bytes.
+// Pass intermediates are W-RHS tiles stored position-major, planar, in quads
+// of positions: positions 4k .. 4k+3 of tile t hold the real parts (RHS-major,
+// each RHS's four values adjacent: 16 W bytes), then the imaginary parts, so
+// an r-block (r a multiple of 8) is one contiguous copy and each warp access
+// is one 16-byte vector per lane, 512 contiguous bytes.  (2D levels keep one
+// position per row: W real parts, then W imaginary parts.)  The host takes W as the
+// RHS count over the ceil(nrhs / 128) tiles, rounded up to a multiple of 32,
+// so a call with fewer than 128 vectors moves only the columns it has.
 //
 // Warp roles (one persistent CTA per SM, looping over work items
-// (node, group, 128-RHS tile)):
+// (node, group, RHS tile)):
 //  * producer warp: TMA bulk copies of each item's block F into a two-slot
 //    ring and of the item's input tile into a shared-memory staging buffer
 //    (one copy per slot for pass intermediates; for the input vectors, 2-D
-//    tensor copies of 128 RHS rows x 128 bytes with the 128-byte swizzle, or
+//    tensor copies of W RHS rows x 128 bytes with the 128-byte swizzle, or
 //    one copy per RHS row when no tensor map could be made); when it issues
 //    item i's copies it also prefetches item
 //    i+1's block and tile into L2, so the staging copy of item i+1 (issued
@@ -88,11 +94,6 @@
 namespace bftc {
 
 constexpr int NR = 128;                  // RHS per work item = MMA M
-constexpr int kEpiWarps = 8;
-constexpr int kMmaWarp = kEpiWarps;
-constexpr int kProdWarp = kEpiWarps + 1;
-constexpr int kPrepWarp = kEpiWarps + 2;
-constexpr int kThreads = (kEpiWarps + 3) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxDim = 64;              // Kin, Nout (complex) per block
 constexpr uint32_t kXr = 0, kXi = 64, kXrl = 128, kXil = 192, kD = 256, kE = 384;
@@ -101,7 +102,23 @@ constexpr uint32_t kSlotBytes = 2u * kMaxDim * kMaxDim * 4u;                  //
 constexpr uint32_t kPointRow = kMaxDim * 8u + 16u;                           // padded staging row
 constexpr uint32_t kStageBytes = (uint32_t)NR * kPointRow;                   // >= Kin * NR * 8
 constexpr uint32_t kTrBytes = 32u * 64u;                                     // per-warp transpose tile
-constexpr size_t kSmemBytes = 2ull * kStages * kSlotBytes + kStageBytes + kEpiWarps * kTrBytes + 256;
+
+// A kernel instance with EPI epilogue warps (8 or 16: EPI / 4 per
+// tensor-memory lane quarter, each taking every (EPI / 4)-th chunk of 8
+// positions or outputs), then the MMA, producer and prep warps.  Tiles of up
+// to 96 RHS run with 16 (their conversions and stores fall on fewer lane
+// quarters, so more warps per quarter hide more latency); 128-RHS tiles with
+// 8 (measured faster there: 3.79 against 4.05 ms per 128-RHS apply at
+// N = 2^20).
+template <int EPI>
+struct Epi {
+    static constexpr int warps = EPI;
+    static constexpr int split = EPI / 4;          // epilogue warps per lane quarter
+    static constexpr int chunks = 64 / 8 / split;  // 8-output chunks of a block per epilogue warp
+    static constexpr int mma_warp = EPI, prod_warp = EPI + 1, prep_warp = EPI + 2;
+    static constexpr int threads = (EPI + 3) * 32;
+    static constexpr size_t smem = 2ull * kStages * kSlotBytes + kStageBytes + EPI * kTrBytes + 256;
+};
 
 enum LoadKind : int { LD_POINTS = 0, LD_SLOTS = 1, LD_GATHER = 2, LD_QUAD = 3 };
 enum StoreKind : int { ST_SLOTS = 0, ST_LOGICAL = 1, ST_POINTS = 2, ST_QUAD = 3 };
@@ -124,6 +141,8 @@ struct alignas(64) TcParams {
     int a, kb, G, ngroups;  // the group's slots differ in node-slot bits a .. a+kb-1
     int Kin, Nout;
     int nrhs;
+    int W;                  // RHS per tile (a multiple of 32, <= NR): tile t holds RHS t W .. t W + W - 1,
+                            // and intermediates are [t][R][re W | im W]
     int split;              // products per real product: 1 plain; 3 hi/lo split; 6 (BF16 only) hi/mid/lo split
     int stall;              // failure-detection test hook: the producer issues no copies, so every
                             // consumer wait runs into its bound and the launch reports BF_ERR_TIMEOUT
@@ -297,11 +316,15 @@ __device__ __forceinline__ int nwork(const TcParams &p, int ntiles) {
 }
 // Work item of this CTA's sub-item s: work items blockIdx.x, + gridDim.x, ..., each
 // taken as nchunks consecutive sub-items (its K-chunks).
-__device__ __forceinline__ int sub_item(const TcParams &p, int s) { return blockIdx.x + (s / nchunks(p)) * gridDim.x; }
+// (Every warp decodes every item, so the common cases avoid integer division.)
+__device__ __forceinline__ int sub_item(const TcParams &p, int s) {
+    return blockIdx.x + (p.q_chunks > 1 ? s / p.q_chunks : s) * gridDim.x;
+}
+__device__ __forceinline__ int chunk_of(const TcParams &p, int s) { return p.q_chunks > 1 ? s % p.q_chunks : 0; }
 __device__ __forceinline__ Item decode(const TcParams &p, int item, int chunk, int ntiles) {
     Item it;
-    it.t = item % ntiles;
-    const int ng = item / ntiles;
+    it.t = ntiles == 1 ? 0 : item % ntiles;
+    const int ng = ntiles == 1 ? item : item / ntiles;
     it.chunk = chunk;
     it.last = chunk == nchunks(p) - 1;
     if (p.load_kind == LD_QUAD) {
@@ -309,21 +332,29 @@ __device__ __forceinline__ Item decode(const TcParams &p, int item, int chunk, i
         it.g = ng / p.q_parts;
         it.part = ng - it.g * p.q_parts;
         it.blk = (long long)ng * nchunks(p) + chunk;
+    } else if ((p.ngroups & (p.ngroups - 1)) == 0) {   // 1D: a power of two
+        it.n = ng >> (__ffs(p.ngroups) - 1);
+        it.g = ng & (p.ngroups - 1);
+        it.part = 0;
+        it.blk = (long long)ng;
     } else {
         it.n = ng / p.ngroups;
         it.g = ng - it.n * p.ngroups;
         it.part = 0;
         it.blk = (long long)it.n * p.ngroups + it.g;
     }
-    it.nt = min(NR, p.nrhs - it.t * NR);
+    it.nt = min(p.W, p.nrhs - it.t * p.W);
     return it;
 }
 // Input staging buffers: two halves of the staging area when an item's tile
-// fits one (2D levels with K-chunks of at most 32 positions), so the next
-// tile's copy overlaps this tile's conversion; else one.
+// fits one (tiles of at most 64 RHS; 2D levels with K-chunks of at most 32
+// positions), so the next tile's copy overlaps this tile's conversion; else
+// one.  Every tile of a launch stages at most Kin positions x p.W RHS.
 constexpr uint32_t kHalfStage = kStageBytes / 2;
 __device__ __forceinline__ int nbufs(const TcParams &p) {
-    return (p.load_kind == LD_QUAD && (uint32_t)p.Kin * NR * 8u <= kHalfStage) ? 2 : 1;
+    const uint32_t need = p.load_kind == LD_POINTS && !p.use_tmap ? (uint32_t)p.W * kPointRow
+                                                                  : (uint32_t)p.Kin * p.W * 8u;
+    return need <= kHalfStage ? 2 : 1;
 }
 // LD_QUAD / ST_QUAD: first input / output block index of the item's group.
 __device__ __forceinline__ long long quad_in_base(const TcParams &p, const Item &w) {
@@ -356,7 +387,8 @@ __device__ __forceinline__ void prefetch_tile_2d(const CUtensorMap *map, int x, 
                  "r"(x), "r"(y)
                  : "memory");
 }
-constexpr uint32_t kBoxBytes = 128u * 128u;   // one tensor-map tile: 128 RHS rows x 128 bytes (16 points)
+// One tensor-map tile: W RHS rows x 128 bytes (16 points).
+__device__ __forceinline__ uint32_t box_bytes(const TcParams &p) { return (uint32_t)p.W * 128u; }
 
 __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
@@ -375,7 +407,7 @@ __device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity) {
 template <class Fn>
 __device__ __forceinline__ void tile_copies(const TcParams &p, const Item &w, int lane, Fn fn) {
     if (p.load_kind == LD_POINTS) {
-        const float2 *src = p.in + (long long)(w.t * NR) * p.ld_in + ((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0;
+        const float2 *src = p.in + (long long)(w.t * p.W) * p.ld_in + ((long long)w.n * p.m + slot_of(p, w.g, 0)) * p.n0;
         for (int row = lane; row < w.nt; row += 32)
             fn((uint32_t)row * kPointRow, src + (long long)row * p.ld_in, (uint32_t)p.Kin * 8u);
     } else if (p.load_kind == LD_QUAD) {
@@ -385,19 +417,19 @@ __device__ __forceinline__ void tile_copies(const TcParams &p, const Item &w, in
         for (int c = c0 + lane; c <= c1; c += 32) {
             const int ka = max(k0, c * p.q_bszi), kb = min(k0 + p.Kin, (c + 1) * p.q_bszi);
             const long long pos = (base + c * p.q_sin) * p.q_bszi + (ka - c * p.q_bszi);
-            fn((uint32_t)(ka - k0) * NR * 8u, p.in + ((long long)w.t * p.R + pos) * NR, (uint32_t)(kb - ka) * NR * 8u);
+            fn((uint32_t)(ka - k0) * p.W * 8u, p.in + ((long long)w.t * p.R + pos) * p.W, (uint32_t)(kb - ka) * p.W * 8u);
         }
     } else {
         for (int j = lane; j < p.G; j += 32)
-            fn((uint32_t)j * p.r * NR * 8u, p.in + ((long long)w.t * p.R + slot_pos(p, w, j)) * NR,
-               (uint32_t)p.r * NR * 8u);
+            fn((uint32_t)j * p.r * p.W * 8u, p.in + ((long long)w.t * p.R + slot_pos(p, w, j)) * p.W,
+               (uint32_t)p.r * p.W * 8u);
     }
 }
 __device__ __forceinline__ uint32_t tile_bytes(const TcParams &p, const Item &w) {
     if (p.load_kind == LD_POINTS)
-        return p.use_tmap ? (uint32_t)(p.Kin / 16) * kBoxBytes : (uint32_t)p.Kin * 8u * (uint32_t)w.nt;
-    if (p.load_kind == LD_QUAD) return (uint32_t)p.Kin * NR * 8u;
-    return (uint32_t)p.r * NR * 8u * (uint32_t)p.G;
+        return p.use_tmap ? (uint32_t)(p.Kin / 16) * box_bytes(p) : (uint32_t)p.Kin * 8u * (uint32_t)w.nt;
+    if (p.load_kind == LD_QUAD) return (uint32_t)p.Kin * p.W * 8u;
+    return (uint32_t)p.r * p.W * 8u * (uint32_t)p.G;
 }
 // Tensor-map coordinates of an LD_POINTS item: x (floats) of its first point, y (row) of its first RHS.
 __device__ __forceinline__ int points_x(const TcParams &p, const Item &w) {
@@ -428,7 +460,7 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
     uint32_t nf = 0, nx = 0;   // factor copies / staging groups issued
     const uint32_t nb = (uint32_t)nbufs(p);
     for (int sub = 0; !p.stall && sub_item(p, sub) < nitems; ++sub) {
-        const Item w = decode(p, sub_item(p, sub), sub % nchunks(p), ntiles);
+        const Item w = decode(p, sub_item(p, sub), chunk_of(p, sub), ntiles);
         const uint32_t slot = nf % kStages, use = nf / kStages;
         bool ok = true;
         if (lane == 0) {
@@ -456,15 +488,15 @@ __device__ __forceinline__ void producer(const TcParams &p, const Smem &s, int n
         unsigned char *xs = s.xs + xb * kHalfStage;
         if (p.load_kind == LD_POINTS && p.use_tmap) {
             if (lane < p.Kin / 16)
-                tma_load_2d(xs + (size_t)lane * kBoxBytes, &p.tmap, points_x(p, w) + 32 * lane, w.t * NR, &s.xfull[xb]);
+                tma_load_2d(xs + (size_t)lane * box_bytes(p), &p.tmap, points_x(p, w) + 32 * lane, w.t * p.W, &s.xfull[xb]);
         } else
             tile_copies(p, w, lane, [&](uint32_t off, const void *src, uint32_t b) { bfk::bulk_g2s(xs + off, src, b, &s.xfull[xb]); });
         ++nx;
         if (sub_item(p, sub + 1) < nitems) {   // next item of this CTA: into L2
-            const Item w2 = decode(p, sub_item(p, sub + 1), (sub + 1) % nchunks(p), ntiles);
+            const Item w2 = decode(p, sub_item(p, sub + 1), chunk_of(p, sub + 1), ntiles);
             if (lane == 0) prefetch_l2(BF ? (const void *)block_src16(p, w2) : (const void *)block_src(p, w2), ubytes);
             if (p.load_kind == LD_POINTS && p.use_tmap) {
-                if (lane < p.Kin / 16) prefetch_tile_2d(&p.tmap, points_x(p, w2) + 32 * lane, w2.t * NR);
+                if (lane < p.Kin / 16) prefetch_tile_2d(&p.tmap, points_x(p, w2) + 32 * lane, w2.t * p.W);
             } else {
                 tile_copies(p, w2, lane, [&](uint32_t, const void *src, uint32_t b) { prefetch_l2(src, b); });
             }
@@ -512,7 +544,7 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
     const uint32_t idesc = idesc_tf32(rows);
     uint32_t it = 0;
     for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
-        const uint32_t acc0 = (sub % nchunks(p)) ? 1u : 0u;   // later K-chunks accumulate
+        const uint32_t acc0 = chunk_of(p, sub) ? 1u : 0u;   // later K-chunks accumulate
         const uint32_t slot = it % kStages;
         const uint32_t b1 = bfk::smem_u32(s.ring) + slot * kSlotBytes;
         const uint32_t bl = bfk::smem_u32(s.blo) + slot * kSlotBytes;
@@ -592,17 +624,17 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
 }
 
 // One part (0 = real, 1 = imaginary) of the staged input tile -> X and X_lo
-// in tensor memory (this thread's RHS lane, positions of its half).
-template <bool BF>
+// in tensor memory (this thread's RHS lane, positions of its half).  WT is
+// the tile width p.W as a compile-time constant (the staged strides).
+template <bool BF, int WT, int SPLIT>
 __device__ __forceinline__ void convert(const TcParams &p, const unsigned char *xs, uint32_t lb, int mlane, int hf,
                                         int part) {
-    const int half = p.Kin >> 1;
     const uint32_t ch = part ? kXi : kXr, cl = part ? kXil : kXrl;
-    for (int e = hf * half; e < (hf + 1) * half; e += 8) {
+    for (int e = 8 * hf; e < p.Kin; e += 8 * SPLIT) {
         float v[8], vl[8];
         if (p.load_kind == LD_POINTS && p.use_tmap) {
             // tile e/16, row mlane (128 B), 16-byte chunk c stored at c ^ (mlane % 8)
-            const unsigned char *row = xs + (size_t)(e >> 4) * kBoxBytes + (size_t)mlane * 128;
+            const unsigned char *row = xs + (size_t)(e >> 4) * (WT * 128) + (size_t)mlane * 128;
             const int c0 = (e & 15) >> 1;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -618,10 +650,15 @@ __device__ __forceinline__ void convert(const TcParams &p, const unsigned char *
                 v[2 * i] = part ? q.y : q.x;
                 v[2 * i + 1] = part ? q.w : q.z;
             }
-        } else {
-            const float *col = reinterpret_cast<const float *>(xs) + (size_t)e * 2 * NR + part * NR + mlane;
+        } else if (p.load_kind == LD_QUAD) {   // planar positions
+            const float *col = reinterpret_cast<const float *>(xs) + (size_t)e * 2 * WT + part * WT + mlane;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = col[(size_t)i * 2 * NR];
+            for (int i = 0; i < 8; ++i) v[i] = col[i * 2 * WT];
+        } else {   // quads of positions: this lane's 4 consecutive values are one 16-byte load
+            const float4 *q4 = reinterpret_cast<const float4 *>(xs) + (size_t)(e >> 2) * 2 * WT + part * WT + mlane;
+            const float4 a = q4[0], b = q4[2 * WT];
+            v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+            v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
         }
         if (BF) {   // BF16 pairs: element e + 2i in the low half of column (e / 2) + i
             uint32_t h[4], m[4], l[4];
@@ -650,17 +687,20 @@ __device__ __forceinline__ void convert(const TcParams &p, const unsigned char *
 }
 
 // Accumulator registers of one thread: its Nout/2 <= 32 outputs, chunks of 8.
+// The outputs of one epilogue warp: chunks o = 8 (hf + SPLIT c) < Nout.
+template <int SPLIT>
 struct Acc {
-    float re[4][8], im[4][8];
+    static constexpr int chunks = 64 / 8 / SPLIT;
+    float re[chunks][8], im[chunks][8];
 };
 
 // D of the item -> registers (D[:, o] into re, D[:, Nout+o] into im).
-__device__ __forceinline__ void read_d(const TcParams &p, uint32_t lb, int hf, Acc &a) {
-    const int half = p.Nout >> 1;
+template <int SPLIT>
+__device__ __forceinline__ void read_d(const TcParams &p, uint32_t lb, int hf, Acc<SPLIT> &a) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int o = hf * half + 8 * c;
-        if (8 * c < half) tmem_ld8x2(lb + kD + (uint32_t)o, lb + kD + (uint32_t)(p.Nout + o), a.re[c], a.im[c]);
+    for (int c = 0; c < Acc<SPLIT>::chunks; ++c) {
+        const int o = 8 * (hf + SPLIT * c);
+        if (o < p.Nout) tmem_ld8x2(lb + kD + (uint32_t)o, lb + kD + (uint32_t)(p.Nout + o), a.re[c], a.im[c]);
     }
 }
 
@@ -668,6 +708,7 @@ __device__ __forceinline__ void read_d(const TcParams &p, uint32_t lb, int hf, A
 // the warp's transpose tile: each lane writes its 64-byte row segment, then
 // each store instruction writes eight rows' 64-byte segments (whole sectors).
 // The tile's 16-byte chunks are XOR-swizzled so both phases are conflict-free.
+template <int WT>
 __device__ __forceinline__ void store_points8(const TcParams &p, const Smem &s, const Item &w, int q, int o,
                                               const float (&re)[8], const float (&im)[8]) {
     const int lane = threadIdx.x & 31;
@@ -683,51 +724,64 @@ __device__ __forceinline__ void store_points8(const TcParams &p, const Smem &s, 
         const int row = 8 * st + (lane >> 2), c = lane & 3;
         const float4 v = tr[row * 4 + (c ^ ((row >> 1) & 3))];
         if (q * 32 + row < w.nt)
-            *reinterpret_cast<float4 *>(p.out + (long long)(w.t * NR + q * 32 + row) * p.ld_out + col + 2 * c) = v;
+            *reinterpret_cast<float4 *>(p.out + (long long)(w.t * WT + q * 32 + row) * p.ld_out + col + 2 * c) = v;
     }
     __syncwarp();
 }
 
-// E of the item, combined with its D (registers) into outputs, stored.
-__device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const Item &w, uint32_t lb, int q, int mlane,
-                                       int hf, Acc &a) {
-    const int half = p.Nout >> 1;
-    const bool live = mlane < w.nt;
+// E of the item combined with its D (registers): Re Y = D[:, o] - E[:, Nout+o],
+// Im Y = D[:, Nout+o] + E[:, o], in place.  After this the E columns are free.
+template <int SPLIT>
+__device__ __forceinline__ void combine_e(const TcParams &p, uint32_t lb, int hf, Acc<SPLIT> &a) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (8 * c >= half) continue;
-        const int o = hf * half + 8 * c;
+    for (int c = 0; c < Acc<SPLIT>::chunks; ++c) {
+        const int o = 8 * (hf + SPLIT * c);
+        if (o >= p.Nout) continue;
         float er[8], ei[8];
         tmem_ld8x2(lb + kE + (uint32_t)o, lb + kE + (uint32_t)(p.Nout + o), er, ei);
-        float re[8], im[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            re[i] = a.re[c][i] - ei[i];
-            im[i] = a.im[c][i] + er[i];
+            a.re[c][i] -= ei[i];
+            a.im[c][i] += er[i];
         }
+    }
+}
+
+// The item's outputs (combined, in registers) stored.
+template <int WT, int SPLIT>
+__device__ __forceinline__ void store_out(const TcParams &p, const Smem &s, const Item &w, int q, int mlane, int hf,
+                                          const Acc<SPLIT> &a) {
+    const bool live = mlane < w.nt;
+#pragma unroll
+    for (int c = 0; c < Acc<SPLIT>::chunks; ++c) {
+        const int o = 8 * (hf + SPLIT * c);
+        if (o >= p.Nout) continue;
+        const float(&re)[8] = a.re[c];
+        const float(&im)[8] = a.im[c];
         if (p.store_kind == ST_POINTS) {
-            store_points8(p, s, w, q, o, re, im);
+            store_points8<WT>(p, s, w, q, o, re, im);
         } else if (p.store_kind == ST_QUAD) {
             if (live) {
                 const long long base = quad_out_base(p, w);
-                float *dst = reinterpret_cast<float *>(p.out) + (long long)w.t * p.R * 2 * NR + mlane;
+                constexpr int W2 = 2 * WT;
+                float *dst = reinterpret_cast<float *>(p.out) + (long long)w.t * p.R * W2 + mlane;
                 const int oo0 = w.part * p.Nout + o;
                 if ((p.q_bszo & 7) == 0) {   // the 8 outputs lie in one block: one index computation
                     const int c = oo0 / p.q_bszo;
                     const long long pos0 = (base + c * p.q_sout) * p.q_bszo + (oo0 - c * p.q_bszo);
-                    float *d0 = dst + pos0 * 2 * NR;
+                    float *d0 = dst + pos0 * W2;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        d0[i * 2 * NR] = re[i];
-                        d0[i * 2 * NR + NR] = im[i];
+                        d0[i * W2] = re[i];
+                        d0[i * W2 + WT] = im[i];
                     }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int oo = oo0 + i, c = oo / p.q_bszo;
                         const long long pos = (base + c * p.q_sout) * p.q_bszo + (oo - c * p.q_bszo);
-                        dst[pos * 2 * NR] = re[i];
-                        dst[pos * 2 * NR + NR] = im[i];
+                        dst[pos * W2] = re[i];
+                        dst[pos * W2 + WT] = im[i];
                     }
                 }
             }
@@ -735,13 +789,74 @@ __device__ __forceinline__ void finish(const TcParams &p, const Smem &s, const I
             const int j = o / p.r, kk = o - j * p.r;
             const int ps = slot_of(p, w.g, j);
             const int blk = p.store_kind == ST_LOGICAL ? bitrev(ps, p.h) : ps;
-            float *dst = reinterpret_cast<float *>(p.out) +
-                         ((long long)w.t * p.R + ((long long)w.n * p.m + blk) * p.r + kk) * 2 * NR + mlane;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                dst[(size_t)i * 2 * NR] = re[i];
-                dst[(size_t)i * 2 * NR + NR] = im[i];
-            }
+            // quads of positions (kk is a multiple of 8): four 16-byte stores
+            const long long pos = (long long)w.t * p.R + ((long long)w.n * p.m + blk) * p.r + kk;
+            float4 *dst = reinterpret_cast<float4 *>(p.out) + (pos >> 2) * 2 * WT + mlane;
+            dst[0] = make_float4(re[0], re[1], re[2], re[3]);
+            dst[WT] = make_float4(im[0], im[1], im[2], im[3]);
+            dst[2 * WT] = make_float4(re[4], re[5], re[6], re[7]);
+            dst[3 * WT] = make_float4(im[4], im[5], im[6], im[7]);
+        }
+    }
+}
+
+// Epilogue warps, per item i (WT = p.W): D of item i-1 into registers; the
+// real half of item i's tile into tensor memory (D(i) may start); E of item
+// i-1 combined into the registers; the imaginary half (E(i) may start, and
+// the staging buffer is released); then item i-1's outputs stored.  The
+// stores come last so that the E chain (E(i-1) done -> E(i) issued) holds
+// only the combine and the conversion, and the next tile's copy overlaps
+// them.
+template <bool BF, int WT, int EPI>
+__device__ __forceinline__ void epilogue(const TcParams &p, const Smem &s, uint32_t tmem, int ntiles, int nitems) {
+    constexpr int SPLIT = Epi<EPI>::split;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int q = warp & 3, hf = warp >> 2;
+    const int mlane = q * 32 + (tid & 31);
+    const uint32_t lb = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t nb = (uint32_t)nbufs(p);
+    // Warps whose lane quarter lies beyond the tile width only keep the
+    // barrier count: their tensor-memory rows are never read out.
+    const bool active = q * 32 < WT;
+    uint32_t it = 0;
+    Item prev{};
+    Acc<SPLIT> acc;
+    for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
+        const Item w = decode(p, sub_item(p, sub), chunk_of(p, sub), ntiles);
+        bool okd = false;
+        if (it > 0) {   // item it-1: D -> registers (its E group is running) once its last K-chunk is in
+            okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
+            tc_fence_after();
+            if (okd && prev.last && active) read_d(p, lb, hf, acc);
+        }
+        const uint32_t xb = it % nb;
+        const unsigned char *xs = s.xs + xb * kHalfStage;
+        const bool okx = warp_wait(&s.xfull[xb], (it / nb) & 1, s.abort_flag, p.err);
+        if (okx && active) convert<BF, WT, SPLIT>(p, xs, lb, mlane, hf, 0);
+        tc_fence_before();
+        warp_arrive(s.xrready);
+        bool oke = false;
+        if (it > 0) {   // item it-1: E combined (item it's D group is running)
+            oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
+            tc_fence_after();
+            if (okd && oke && prev.last && active) combine_e(p, lb, hf, acc);
+        }
+        if (okx && active) convert<BF, WT, SPLIT>(p, xs, lb, mlane, hf, 1);
+        tc_fence_before();
+        warp_arrive(s.xiready);
+        warp_arrive(&s.xfree[xb]);
+        if (okd && oke && prev.last && active) store_out<WT, SPLIT>(p, s, prev, q, mlane, hf, acc);   // item it-1's outputs
+        prev = w;
+    }
+    if (it > 0) {
+        const bool okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
+        tc_fence_after();
+        if (okd && active) read_d(p, lb, hf, acc);
+        const bool oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
+        tc_fence_after();
+        if (okd && oke && active) {
+            combine_e(p, lb, hf, acc);
+            store_out<WT, SPLIT>(p, s, prev, q, mlane, hf, acc);
         }
     }
 }
@@ -781,15 +896,15 @@ __global__ void bf16_split_kernel(const float *fac, uint4 *out, long long nblock
 }
 
 // BF: the BF16 rungs (p.bf16 = 1) or the TF32 rungs, one instantiation each.
-template <bool BF>
-__global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constant__ TcParams p) {
+template <bool BF, int EPI>
+__global__ void __launch_bounds__(Epi<EPI>::threads, 1) bf_tc_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem s;
     s.ring = reinterpret_cast<float *>(smem_raw);
     s.blo = s.ring + (size_t)kStages * (kSlotBytes / 4);
     s.xs = reinterpret_cast<unsigned char *>(s.blo + (size_t)kStages * (kSlotBytes / 4));
     s.tr = reinterpret_cast<float4 *>(s.xs + kStageBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s.xs + kStageBytes + kEpiWarps * kTrBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s.xs + kStageBytes + EPI * kTrBytes);
     s.full = bars;
     s.empty = bars + kStages;
     s.bready = bars + 2 * kStages;
@@ -810,10 +925,10 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
         }
         for (int b = 0; b < 2; ++b) {
             bfk::mbar_init(&s.xfull[b], 1);
-            bfk::mbar_init(&s.xfree[b], kEpiWarps);
+            bfk::mbar_init(&s.xfree[b], EPI);
         }
-        bfk::mbar_init(s.xrready, kEpiWarps);
-        bfk::mbar_init(s.xiready, kEpiWarps);
+        bfk::mbar_init(s.xrready, EPI);
+        bfk::mbar_init(s.xiready, EPI);
         bfk::mbar_init(s.ddone, 1);
         bfk::mbar_init(s.edone, 1);
         *s.abort_flag = 0;
@@ -830,55 +945,23 @@ __global__ void __launch_bounds__(kThreads, 1) bf_tc_kernel(const __grid_constan
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s.tmem_slot;
-    const int ntiles = (p.nrhs + NR - 1) / NR;
+    const int ntiles = (p.nrhs + p.W - 1) / p.W;
     const int nitems = nwork(p, ntiles);
-    if (warp == kProdWarp) {
+    if (warp == Epi<EPI>::prod_warp) {
         producer<BF>(p, s, ntiles, nitems);
-    } else if (warp == kPrepWarp) {
+    } else if (warp == Epi<EPI>::prep_warp) {
         prep<BF>(p, s, nitems);
-    } else if (warp == kMmaWarp) {
+    } else if (warp == Epi<EPI>::mma_warp) {
         if ((tid & 31) == 0) mma_issuer<BF>(p, s, tmem, nitems);
-    } else {
-        const int q = warp & 3, hf = warp >> 2;
-        const int mlane = q * 32 + (tid & 31);
-        const uint32_t lb = tmem + ((uint32_t)(q * 32) << 16);
-        const uint32_t nb = (uint32_t)nbufs(p);
-        uint32_t it = 0;
-        Item prev{};
-        Acc acc;
-        for (int sub = 0; sub_item(p, sub) < nitems; ++sub, ++it) {
-            const Item w = decode(p, sub_item(p, sub), sub % nchunks(p), ntiles);
-            bool okd = false;
-            if (it > 0) {   // item it-1: D -> registers (its E group is running) once its last K-chunk is in
-                okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
-                tc_fence_after();
-                if (okd && prev.last) read_d(p, lb, hf, acc);
-            }
-            const uint32_t xb = it % nb;
-            const unsigned char *xs = s.xs + xb * kHalfStage;
-            const bool okx = warp_wait(&s.xfull[xb], (it / nb) & 1, s.abort_flag, p.err);
-            if (okx) convert<BF>(p, xs, lb, mlane, hf, 0);
-            tc_fence_before();
-            warp_arrive(s.xrready);
-            if (it > 0) {   // item it-1: E, combine, store (item it's D group is running)
-                const bool oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
-                tc_fence_after();
-                if (okd && oke && prev.last) finish(p, s, prev, lb, q, mlane, hf, acc);
-            }
-            if (okx) convert<BF>(p, xs, lb, mlane, hf, 1);
-            tc_fence_before();
-            warp_arrive(s.xiready);
-            warp_arrive(&s.xfree[xb]);
-            prev = w;
-        }
-        if (it > 0) {
-            const bool okd = warp_wait(s.ddone, (it - 1) & 1, s.abort_flag, p.err);
-            tc_fence_after();
-            if (okd) read_d(p, lb, hf, acc);
-            const bool oke = warp_wait(s.edone, (it - 1) & 1, s.abort_flag, p.err);
-            tc_fence_after();
-            if (okd && oke) finish(p, s, prev, lb, q, mlane, hf, acc);
-        }
+    } else if (EPI == 16) {   // tiles of 32, 64 or 96 RHS
+        if (p.W == 32)
+            epilogue<BF, 32, EPI>(p, s, tmem, ntiles, nitems);
+        else if (p.W == 64)
+            epilogue<BF, 64, EPI>(p, s, tmem, ntiles, nitems);
+        else
+            epilogue<BF, 96, EPI>(p, s, tmem, ntiles, nitems);
+    } else {                  // 128-RHS tiles
+        epilogue<BF, NR, EPI>(p, s, tmem, ntiles, nitems);
     }
     tc_fence_before();
     __syncthreads();

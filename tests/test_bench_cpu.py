@@ -77,3 +77,25 @@ def test_reference_arm_other_ranks_exit_silently():
 def test_warmup_below_three_is_rejected():
     r = _bench(["--impl", "reference", "--workload", "fio_n4096_r12", "--steps", "1", "--warmup", "2"])
     assert r.returncode != 0
+
+
+def test_tensor_core_traffic_model_follows_the_tile_width():
+    """The bytes the benchmark charges a tensor-core apply: 8 two-level passes
+    at N = 2^20, L = 16, leaf 16, r = 16 read 16384 dense 64 x 64 complex
+    blocks each (32 KB, once per RHS tile), the caller's vectors in and out,
+    and 7 intermediates of R = 2^20 positions written and read, W RHS wide."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class F:
+        L, n0, r, h, m, N = 16, 16, 16, 8, 256, 1 << 20
+
+    R = (1 << F.L) * F.r
+    blocks = 8 * 16384 * 32768
+    for nrhs, W in ((128, 128), (32, 32), (20, 32), (64, 64)):
+        assert bench.tc_tile_width(nrhs) == W
+        assert bench.tc_traffic_bytes(F, nrhs) == blocks + 8 * nrhs * 2 * F.N + 8 * W * 2 * R * 7
+    assert abs(bench.tc_traffic_bytes(F, 128) / 1e9 - 21.47) < 0.01
+    # several tiles: evened out, whole warps
+    assert [bench.tc_tile_width(n) for n in (1, 33, 100, 129, 200, 257)] == [32, 64, 128, 96, 128, 96]
+    assert bench.tc_traffic_bytes(F, 256) == 2 * blocks + 8 * 256 * 2 * F.N + 8 * 256 * 2 * R * 7

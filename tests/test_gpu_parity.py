@@ -112,11 +112,12 @@ TC_SHAPES = [(0, 16, 16), (2, 16, 16), (4, 16, 32), (6, 32, 16), (8, 16, 16), (8
 @pytest.mark.parametrize("L,n0,r", TC_SHAPES)
 @pytest.mark.parametrize("kmax", [None, 1])
 def test_tensor_core_path(bf, L, n0, r, kmax, monkeypatch):
-    """Batches on the tcgen05 core (dense per-group blocks, 128 RHS per work
-    item, 3xTF32; forced here for every batch size): groups of 1, 2 and 4
-    slots, ragged RHS tiles, several tiles, and one slot bit per pass
-    (kmax = 1).  Shapes whose blocks exceed 64 x 64 (n0 = 64) fall back to
-    the CUDA-core core."""
+    """Batches on the tcgen05 core (dense per-group blocks, RHS tiles of 32 to
+    128, 3xTF32; forced here for every batch size): groups of 1, 2 and 4
+    slots, ragged RHS tiles and tile widths 32 (8 vectors), 64 (57), 96 (130:
+    two tiles) and 128 (300: three), and one slot bit per pass (kmax = 1).
+    Shapes whose blocks exceed 64 x 64 (n0 = 64) fall back to the CUDA-core
+    core."""
     from bfinputs import complex_normal, synthetic_factors
     monkeypatch.setenv("BF_TC", "1")
     monkeypatch.setenv("BF_TC_MIN", "1")      # every batch on the tensor-core core
@@ -124,7 +125,7 @@ def test_tensor_core_path(bf, L, n0, r, kmax, monkeypatch):
         monkeypatch.setenv("BF_TC_KMAX", str(kmax))
     F = synthetic_factors(L, n0, r, seed=500 + L + r, dtype=np.complex64)
     plan = bf.bf_plan_create(F, nrhs_max=300)
-    for nrhs in (8, 130, 300):
+    for nrhs in (8, 57, 130, 300):
         g = complex_normal((nrhs, F.N), seed=nrhs + 3, dtype=np.complex64)
         assert _rel(_run(bf, plan, g), _oracle(F, g)) < TOL
         assert _rel(_run(bf, plan, g, adjoint=True), _oracle(F, g, True)) < TOL
@@ -300,11 +301,17 @@ def test_full_size_n1m_r16_tensor_core_batch(bf):
     rhs = np.einsum("ij,ij->i", g.astype(np.complex128), np.conj(a.astype(np.complex128)))
     scale = np.linalg.norm(u, axis=1) * np.linalg.norm(f, axis=1)
     assert np.max(np.abs(lhs - rhs) / scale) < TOL
+    # 32 vectors (the benchmark sweep's 32-RHS point): one 32-wide tile
+    u32 = _run(bf, plan, g[:32])
+    a32 = _run(bf, plan, f[:32], adjoint=True)
+    for j in (0, 31):
+        assert _rel(u32[j], capply.bf_apply_c(P, g[j])) < TOL
+        assert _rel(a32[j], capply.bf_adjoint_c(P, f[j])) < TOL
     plan.destroy()
 
 
-@pytest.mark.parametrize("adjoint", [False, True])
-def test_precision_ladder_tensor_core(bf, adjoint):
+@pytest.mark.parametrize("adjoint,nrhs", [(False, 128), (True, 128), (False, 40)])
+def test_precision_ladder_tensor_core(bf, adjoint, nrhs):
     """The tensor-core core's five rungs at N = 2^16, L = 12, r = 16, 128 RHS,
     forward and adjoint, against the FP64 C oracle on sampled columns.  The
     FP32-level rungs (3xTF32, the default, and the BF16 three-way split) are
@@ -312,21 +319,22 @@ def test_precision_ladder_tensor_core(bf, adjoint):
     put them, well above the FP32 bar and well below 1: plain TF32 (11 bits,
     ~1e-3), the BF16 hi/lo split (16 bits, ~1e-5) and plain BF16 (8 bits,
     ~6e-3).  The order of the rungs pins that each one really forms the
-    products it claims."""
+    products it claims.  40 vectors run as one 64-wide tile."""
     from bfinputs import complex_normal, synthetic_factors
     from oracle import capply
     from paper_1502_01379_gb300 import capi
     F = synthetic_factors(12, 16, 16, seed=4, dtype=np.complex64)
     plan = bf.bf_plan_create(F, nrhs_max=128)
-    g = complex_normal((128, F.N), seed=8, dtype=np.complex64)
+    g = complex_normal((nrhs, F.N), seed=8, dtype=np.complex64)
     P = capply.PreparedFactors(F)
     fn = capply.bf_adjoint_c if adjoint else capply.bf_apply_c
-    ref = [fn(P, g[j]) for j in (0, 77, 127)]
+    cols = (0, nrhs * 3 // 5, nrhs - 1)
+    ref = [fn(P, g[j]) for j in cols]
     errs = {}
     for prec in (capi.BF_PREC_FP32, capi.BF_PREC_TF32, capi.BF_PREC_BF16X6, capi.BF_PREC_BF16X3, capi.BF_PREC_BF16):
         capi.bf_plan_set_precision(plan, prec)
         u = _run(bf, plan, g, adjoint=adjoint)
-        errs[prec] = max(_rel(u[j], r) for j, r in zip((0, 77, 127), ref))
+        errs[prec] = max(_rel(u[j], r) for j, r in zip(cols, ref))
     assert errs[capi.BF_PREC_FP32] < TOL
     assert errs[capi.BF_PREC_BF16X6] < TOL
     assert 1e-4 < errs[capi.BF_PREC_TF32] < 1e-2
