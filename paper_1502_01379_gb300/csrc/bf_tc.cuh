@@ -57,9 +57,9 @@
 // each RHS's four values adjacent: 16 W bytes), then the imaginary parts, so
 // an r-block (r a multiple of 8) is one contiguous copy and each warp access
 // is one 16-byte vector per lane, 512 contiguous bytes.  (2D levels keep one
-// position per row: W real parts, then W imaginary parts.)  The host takes W as the
-// RHS count over the ceil(nrhs / 128) tiles, rounded up to a multiple of 32,
-// so a call with fewer than 128 vectors moves only the columns it has.
+// position per row: W real parts, then W imaginary parts.)  The host takes W
+// as the RHS count over the ceil(nrhs / 128) tiles, rounded up to a multiple
+// of 32, so a call with fewer than 128 vectors moves only the columns it has.
 //
 // Warp roles (one persistent CTA per SM, looping over work items
 // (node, group, RHS tile)):
@@ -141,8 +141,8 @@ struct alignas(64) TcParams {
     int a, kb, G, ngroups;  // the group's slots differ in node-slot bits a .. a+kb-1
     int Kin, Nout;
     int nrhs;
-    int W;                  // RHS per tile (a multiple of 32, <= NR): tile t holds RHS t W .. t W + W - 1,
-                            // and intermediates are [t][R][re W | im W]
+    int W;                  // RHS per tile (a multiple of 32, <= NR): tile t holds RHS t W .. t W + W - 1;
+                            // intermediates hold R positions x W RHS per tile (layout above)
     int split;              // products per real product: 1 plain; 3 hi/lo split; 6 (BF16 only) hi/mid/lo split
     int stall;              // failure-detection test hook: the producer issues no copies, so every
                             // consumer wait runs into its bound and the launch reports BF_ERR_TIMEOUT
@@ -347,9 +347,9 @@ __device__ __forceinline__ Item decode(const TcParams &p, int item, int chunk, i
     return it;
 }
 // Input staging buffers: two halves of the staging area when an item's tile
-// fits one (tiles of at most 64 RHS; 2D levels with K-chunks of at most 32
-// positions), so the next tile's copy overlaps this tile's conversion; else
-// one.  Every tile of a launch stages at most Kin positions x p.W RHS.
+// (Kin positions x p.W RHS) fits one -- tiles of up to 64 RHS, and passes or
+// 2D K-chunks of at most 32 positions -- so the next tile's copy overlaps this
+// tile's conversion; else one.
 constexpr uint32_t kHalfStage = kStageBytes / 2;
 __device__ __forceinline__ int nbufs(const TcParams &p) {
     const uint32_t need = p.load_kind == LD_POINTS && !p.use_tmap ? (uint32_t)p.W * kPointRow
@@ -624,8 +624,9 @@ __device__ __forceinline__ void mma_issuer(const TcParams &p, const Smem &s, uin
 }
 
 // One part (0 = real, 1 = imaginary) of the staged input tile -> X and X_lo
-// in tensor memory (this thread's RHS lane, positions of its half).  WT is
-// the tile width p.W as a compile-time constant (the staged strides).
+// in tensor memory (this thread's RHS lane; the warp's chunks of 8 positions,
+// e = 8 (hf + SPLIT c)).  WT is the tile width p.W as a compile-time constant
+// (the staged strides).
 template <bool BF, int WT, int SPLIT>
 __device__ __forceinline__ void convert(const TcParams &p, const unsigned char *xs, uint32_t lb, int mlane, int hf,
                                         int part) {
@@ -686,8 +687,8 @@ __device__ __forceinline__ void convert(const TcParams &p, const unsigned char *
     tmem_wait_st();
 }
 
-// Accumulator registers of one thread: its Nout/2 <= 32 outputs, chunks of 8.
-// The outputs of one epilogue warp: chunks o = 8 (hf + SPLIT c) < Nout.
+// Accumulator registers of one thread: the outputs of its warp's chunks
+// o = 8 (hf + SPLIT c) < Nout, eight per chunk.
 template <int SPLIT>
 struct Acc {
     static constexpr int chunks = 64 / 8 / SPLIT;
