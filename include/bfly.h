@@ -102,7 +102,10 @@ bf_status bf_plan_create(bf_plan *plan, const bf_desc *desc, const bf_factors *f
  *            Device pointers are used in place.  Host pointers (pinned or
  *            pageable) are staged through plan-owned device buffers, which the
  *            first such call allocates; the host output is complete when
- *            `stream` completes.
+ *            `stream` completes.  On the single-vector path the copies run
+ *            per group of tree nodes on plan-owned side streams forked from
+ *            and joined back to `stream` (also under graph capture), so they
+ *            overlap the other groups' kernels.
  *   nrhs     >= 0; 0 is a no-op.  Processed nrhs_max vectors per pass: one
  *            vector at a time through the fused single-RHS kernels (up to 4
  *            per thread block), 8..31 through the CUDA-core multi-RHS core,

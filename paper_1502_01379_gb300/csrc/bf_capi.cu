@@ -83,6 +83,10 @@ struct bf_plan_s {
     Direction fwd, adj;
     float2 *d_ws = nullptr;                       // R x nrhs_max level-h vectors
     float2 *d_stage_in = nullptr, *d_stage_out = nullptr;  // host-pointer staging, N x nrhs_max
+    // host-pointer calls on the fused path: node groups on side streams (created on first use)
+    static constexpr int kGroups = 4;
+    cudaStream_t gstream[kGroups] = {};
+    cudaEvent_t gfork = nullptr, gjoin[kGroups] = {};
     unsigned *d_err = nullptr;
     size_t device_bytes = 0;
     bool profiling = false;
@@ -744,6 +748,11 @@ void free_plan(bf_plan_s *P) {
     cudaFree(P->d_ws);
     cudaFree(P->d_stage_in);
     cudaFree(P->d_stage_out);
+    for (int g = 0; g < bf_plan_s::kGroups; ++g) {
+        if (P->gstream[g]) cudaStreamDestroy(P->gstream[g]);
+        if (P->gjoin[g]) cudaEventDestroy(P->gjoin[g]);
+    }
+    if (P->gfork) cudaEventDestroy(P->gfork);
     cudaFree(P->d_err);
     for (auto &t : P->timings) {
         cudaEventDestroy(t.a);
@@ -877,6 +886,105 @@ bf_status ensure_staging(bf_plan_s &P) {
     return BF_OK;
 }
 
+// Side streams and events of the overlapped host-buffer path.
+bf_status ensure_groups(bf_plan_s &P) {
+    if (P.gfork) return BF_OK;
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int g = 0; g < bf_plan_s::kGroups && e == cudaSuccess; ++g) {
+        e = cudaStreamCreateWithFlags(&P.gstream[g], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.gjoin[g], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        for (int g = 0; g < bf_plan_s::kGroups; ++g) {
+            if (P.gstream[g]) cudaStreamDestroy(P.gstream[g]);
+            if (P.gjoin[g]) cudaEventDestroy(P.gjoin[g]);
+            P.gstream[g] = nullptr;
+            P.gjoin[g] = nullptr;
+        }
+        if (fork) cudaEventDestroy(fork);
+        return cuda_fail(e);
+    }
+    P.gfork = fork;
+    return BF_OK;
+}
+
+// The fused path with host buffers, its copies overlapping the kernels.  The
+// m tree nodes split into G groups of consecutive nodes, each on a side
+// stream forked from the caller's: the group's input points are copied in
+// and its down-kernel CTAs run; after the join (the up half needs every
+// node's segment), each group's up-kernel CTAs run and its output points are
+// copied back on the same side stream, and the caller's stream joins them.
+// Every node-dependent address in the kernels is linear in the node index
+// (input and output points, factor chunk, level-h segment, the M^h gather and
+// S row), so a group is the same kernel on pointers shifted by its first node;
+// the checked build's extents shrink by the same offsets.  `src` / `dst` are
+// the caller's host pointers (ld) or device pointers, as host_in / host_out say.
+template <int T>
+cudaError_t launch_pair_groups(const bf_plan_s &P, const Direction &D, const float2 *src, bool host_in, float2 *dst,
+                               bool host_out, long long ld, int nrhs, cudaStream_t s) {
+    const int G = (int)std::min<long long>(bf_plan_s::kGroups, P.m), per = P.m / G;
+    const long long npts = P.N / P.m, nseg = (long long)P.m * P.r;   // points per node, segment length
+    const dim3 grid((nrhs + T - 1) / T, per);
+    const dim3 block(P.consumers + 32);
+    const size_t smem = plan_smem(P, T);
+    const float2 *din = host_in ? P.d_stage_in : src;
+    const long long ld_in = host_in ? P.N : ld;
+    float2 *dout = host_out ? P.d_stage_out : dst;
+    const long long ld_out = host_out ? P.N : ld;
+    cudaError_t e = cudaEventRecord(P.gfork, s);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const long long n0 = (long long)g * per;
+        cudaStream_t gs = P.gstream[g];
+        e = cudaStreamWaitEvent(gs, P.gfork, 0);
+        if (e == cudaSuccess && host_in)
+            e = cudaMemcpy2DAsync(P.d_stage_in + n0 * npts, P.N * 8, src + n0 * npts, ld * 8, per * npts * 8, nrhs,
+                                  cudaMemcpyHostToDevice, gs);
+        if (e != cudaSuccess) break;
+        Params pd = base_params(P, D.down);
+        pd.fac += n0 * pd.cta_len;
+        pd.fac_elems -= n0 * pd.cta_len;
+        pd.in = din + n0 * npts;
+        pd.ld_in = ld_in;
+        pd.out = P.d_ws + n0 * nseg;
+        pd.ld_out = P.R;
+        pd.nrhs = nrhs;
+        pd.in_elems = (long long)(nrhs - 1) * ld_in + P.N - n0 * npts;
+        pd.out_elems = P.R * ws_rhs(P) - n0 * nseg;
+        bfk::bf_down_kernel<T><<<grid, block, smem, gs>>>(pd);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(P.gjoin[g], gs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P.gjoin[g], 0);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(P.gfork, s);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const long long n0 = (long long)g * per;
+        cudaStream_t gs = P.gstream[g];
+        e = cudaStreamWaitEvent(gs, P.gfork, 0);
+        if (e != cudaSuccess) break;
+        Params pu = base_params(P, D.up);
+        pu.fac += n0 * pu.cta_len;
+        pu.fac_elems -= n0 * pu.cta_len;
+        pu.in = P.d_ws + n0 * P.r;
+        pu.ld_in = P.R;
+        pu.S = D.d_S + n0 * nseg;
+        pu.s_elems -= n0 * nseg;
+        pu.out = dout + n0 * npts;
+        pu.ld_out = ld_out;
+        pu.nrhs = nrhs;
+        pu.in_elems = P.R * ws_rhs(P) - n0 * P.r;
+        pu.out_elems = (long long)(nrhs - 1) * ld_out + P.N - n0 * npts;
+        bfk::bf_up_kernel<T><<<grid, block, smem, gs>>>(pu);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && host_out)
+            e = cudaMemcpy2DAsync(dst + n0 * npts, ld * 8, P.d_stage_out + n0 * npts, P.N * 8, per * npts * 8, nrhs,
+                                  cudaMemcpyDeviceToHost, gs);
+        if (e == cudaSuccess) e = cudaEventRecord(P.gjoin[g], gs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P.gjoin[g], 0);
+    }
+    return e;
+}
+
 bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cudaStream_t s, bool adjoint) {
     bfint::NvtxRange range(adjoint ? "bf_apply_adjoint" : "bf_apply");
     if (!P || !in || !out || nrhs < 0 || ld < P->N) return BF_ERR_INVALID;
@@ -897,6 +1005,18 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         const float2 *src = static_cast<const float2 *>(in) + (long long)c0 * ld;
         float2 *dst = static_cast<float2 *>(out) + (long long)c0 * ld;
         long long ld_in = ld, ld_out = ld;
+        const bool fused = !(P->tc && nc >= P->tc_min) && !(P->wide && nc >= P->wide_min);
+        if (fused && (host_in || host_out) && !P->profiling && P->m >= 2) {   // copies overlap the kernels
+            const bf_status st = ensure_groups(*P);
+            if (st != BF_OK) return st;
+            const int T = pick_T(*P, nc);
+            const cudaError_t e =
+                T == 4 ? launch_pair_groups<4>(*P, D, src, host_in, dst, host_out, ld, nc, s)
+                : T == 2 ? launch_pair_groups<2>(*P, D, src, host_in, dst, host_out, ld, nc, s)
+                         : launch_pair_groups<1>(*P, D, src, host_in, dst, host_out, ld, nc, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            continue;
+        }
         if (host_in) {
             if (ld == P->N)   // contiguous columns: one plain copy
                 BF_CUDA(cudaMemcpyAsync(P->d_stage_in, src, (size_t)nc * P->N * 8, cudaMemcpyHostToDevice, s));
@@ -911,7 +1031,7 @@ bf_status run(bf_plan P, const void *in, void *out, int nrhs, long long ld, cuda
         Timing *tm = next_timing(*P);
         cudaError_t e;
         if (P->tc && nc >= P->tc_min) {
-            // tensor-core multi-RHS core (128 RHS per work item).  Its TMA row
+            // tensor-core multi-RHS core (RHS tiles of 32-128).  Its TMA row
             // copies and 16-byte stores need aligned vectors with an even leading
             // dimension; others go through the (aligned) staging buffers.
             auto aligned = [](const void *q, long long l) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0 && (l & 1) == 0; };
