@@ -265,6 +265,24 @@ def test_host_buffers_overlapped_groups(bf):
     plan.destroy()
 
 
+@pytest.mark.parametrize("L,n0,r", [(0, 5, 3), (2, 4, 3), (4, 3, 5)])
+def test_host_buffers_shallow_trees(bf, L, n0, r):
+    """The host-buffer path on trees with fewer than four middle-level nodes
+    (m = 1: one launch; m = 2: two groups of one node; m = 4: four of one),
+    forward and adjoint, against the FP64 oracle."""
+    from bfinputs import complex_normal, synthetic_factors
+    F = synthetic_factors(L, n0, r, seed=40 + L, dtype=np.complex64)
+    plan = bf.bf_plan_create(F, nrhs_max=2)
+    g = complex_normal((3, F.N), seed=41 + L, dtype=np.complex64)
+    for adjoint in (False, True):
+        out = np.zeros_like(g)
+        (bf.bf_apply_adjoint if adjoint else bf.bf_apply)(plan, g, out, nrhs=3)
+        torch.cuda.synchronize()
+        assert _rel(out, _oracle(F, g, adjoint)) < TOL
+    bf.bf_plan_check(plan)
+    plan.destroy()
+
+
 def test_adjoint_identity_fp32(bf):
     """<K g, f> = <g, K^* f> for the GPU apply and adjoint (FP32)."""
     from bfinputs import complex_normal, synthetic_factors
